@@ -1,0 +1,171 @@
+"""Seeded synthetic inputs shaped like the paper's LJ workloads.
+
+This module holds no arithmetic of the MD method (no forces, no integration, no
+neighbour search): it only draws initial conditions and parameter tables.  It is
+the one module that both the CUDA path's callers and the CPU oracle's callers
+use, so that both sides see bit-identical inputs.
+
+Recipe (paper silent on all of it; the paper's own LJ benchmark is a
+synthetic liquid, Section 5):
+  * FCC lattice with n = ceil((N/4)^(1/3)) unit cells per side in a cubic box
+    of side L = (N/rho)^(1/3); if 4 n^3 > N a seeded subset of N sites is kept
+    (in lattice order); the lattice is offset by a/4 so no site sits on a face;
+  * uniform jitter in [-jitter, +jitter) per component (default 0.05 sigma);
+  * velocities N(0, sqrt(T/m)) per component, mean removed, then rescaled so
+    that 2K/(3N-3) equals T exactly;
+  * Kob-Andersen types: exactly round(0.8 N) type A (0) in a seeded random
+    permutation, the rest type B (1);
+  * numpy PCG64 streams spawned from one seed; base seed 20130826, replica or
+    request k uses base + k.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 20130826
+
+
+@dataclass
+class PairTable:
+    """Per type-pair eps, sigma, r_cut (ntypes x ntypes, symmetric)."""
+    eps: np.ndarray
+    sigma: np.ndarray
+    rcut: np.ndarray
+
+    @property
+    def ntypes(self) -> int:
+        return int(self.eps.shape[0])
+
+    def as_dict(self):
+        return {"eps": self.eps, "sigma": self.sigma, "rcut": self.rcut}
+
+
+def lj_single(eps=1.0, sigma=1.0, rcut=2.5) -> PairTable:
+    one = np.ones((1, 1))
+    return PairTable(eps * one, sigma * one, rcut * one)
+
+
+def kob_andersen(rcut_over_sigma=2.5) -> PairTable:
+    """Kob-Andersen 80:20 binary mixture, r_cut = 2.5 sigma_ij."""
+    eps = np.array([[1.0, 1.5], [1.5, 0.5]])
+    sig = np.array([[1.0, 0.8], [0.8, 0.88]])
+    return PairTable(eps, sig, rcut_over_sigma * sig)
+
+
+@dataclass
+class Workload:
+    """One LJ system: initial state plus run parameters (tag order)."""
+    pos: np.ndarray            # (N, 3) float64
+    vel: np.ndarray            # (N, 3) float64
+    types: np.ndarray          # (N,) int32
+    box: np.ndarray            # (3,) float64
+    pairs: PairTable
+    r_buff: float = 0.4
+    dt: float = 0.005
+    mass: float = 1.0
+    seed: int = BASE_SEED
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+
+def _streams(seed: int, k: int):
+    return [np.random.Generator(np.random.PCG64(s)) for s in np.random.SeedSequence(seed).spawn(k)]
+
+
+def fcc_positions(n: int, rho: float, rng: np.random.Generator, jitter: float = 0.05):
+    """FCC sites (subset if needed) + uniform jitter in a centred cubic box."""
+    if n < 1:
+        return np.zeros((0, 3)), np.full(3, 1.0)
+    L = (n / rho) ** (1.0 / 3.0)
+    m = int(math.ceil((n / 4.0) ** (1.0 / 3.0) - 1e-9))
+    a = L / m
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    g = np.arange(m)
+    cells = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    sites = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3) * a
+    if sites.shape[0] > n:
+        keep = np.sort(rng.choice(sites.shape[0], size=n, replace=False))
+        sites = sites[keep]
+    pos = sites - 0.5 * L + 0.25 * a
+    pos = pos + rng.uniform(-jitter, jitter, size=pos.shape)
+    return pos, np.full(3, L)
+
+
+def maxwell_boltzmann(n: int, T: float, mass: float, rng: np.random.Generator):
+    """Gaussian velocities, zero net momentum, rescaled to 2K/(3N-3) = T."""
+    v = rng.normal(0.0, math.sqrt(T / mass), size=(n, 3))
+    if n < 2:
+        return np.zeros((n, 3))
+    v -= v.mean(axis=0)
+    k = 0.5 * mass * float(np.sum(v * v))
+    v *= math.sqrt(T * (3 * n - 3) / (2.0 * k))
+    return v
+
+
+def ka_types(n: int, rng: np.random.Generator, frac_a: float = 0.8):
+    t = np.ones(n, np.int32)
+    t[: int(round(frac_a * n))] = 0
+    return rng.permutation(t).astype(np.int32)
+
+
+def lj_fluid(n: int, rho: float, T: float, seed: int = BASE_SEED, pairs: PairTable | None = None,
+             r_buff: float = 0.4, dt: float = 0.005, mass: float = 1.0, jitter: float = 0.05,
+             binary: bool = False) -> Workload:
+    rp, rv, rt = _streams(seed, 3)
+    pos, box = fcc_positions(n, rho, rp, jitter)
+    vel = maxwell_boltzmann(n, T, mass, rv)
+    types = ka_types(n, rt) if binary else np.zeros(n, np.int32)
+    pairs = pairs or (kob_andersen() if binary else lj_single())
+    return Workload(pos, vel, types, box, pairs, r_buff, dt, mass, seed,
+                    {"rho": rho, "T": T, "jitter": jitter})
+
+
+# --- the five workload shapes -------------------------------------------------
+
+def plain_fp64_4k(seed: int = BASE_SEED) -> Workload:
+    """LJ fluid N=4,000, rho 0.84, T 1.2, r_cut 2.5 (shifted), r_buff 0.4, dt 0.005."""
+    return lj_fluid(4000, 0.84, 1.2, seed)
+
+
+def lj_64k(seed: int = BASE_SEED) -> Workload:
+    """LJ fluid N=64,000, rho 0.84, T 1.2, r_cut 2.5, r_buff 0.4, dt 0.005."""
+    return lj_fluid(64000, 0.84, 1.2, seed)
+
+
+def ka_1m(seed: int = BASE_SEED, n: int = 1_000_000) -> Workload:
+    """Kob-Andersen 80:20, N=10^6, rho 1.2, T 1.0, r_cut 2.5 sigma_ij, r_buff 0.3."""
+    return lj_fluid(n, 1.2, 1.0, seed, binary=True, r_buff=0.3)
+
+
+def replica_params(count: int = 256, seed: int = BASE_SEED, n_lo: int = 500, n_hi: int = 20000):
+    """(N_k, rho_k, T_k, seed_k) for the batched-ensemble shape."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), count))).astype(int)
+    rhos = rng.uniform(0.7, 0.9, count)
+    ts = rng.uniform(0.8, 1.5, count)
+    return [(int(ns[k]), float(rhos[k]), float(ts[k]), seed + 1 + k) for k in range(count)]
+
+
+def replica(n: int, rho: float, T: float, seed: int) -> Workload:
+    return lj_fluid(n, rho, T, seed, r_buff=0.4)
+
+
+def request_trace(count: int = 1000, rate: float = 50.0, seed: int = BASE_SEED,
+                  n_lo: int = 256, n_hi: int = 200000, steps_lo: int = 1000,
+                  steps_hi: int = 50000):
+    """Poisson arrival trace: list of dicts(arrival, n, rho, T, steps, seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7))
+    gaps = rng.exponential(1.0 / rate, count)
+    t = np.cumsum(gaps)
+    ns = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), count))).astype(int)
+    rhos = rng.uniform(0.7, 0.9, count)
+    ts = rng.uniform(0.8, 1.5, count)
+    steps = rng.integers(steps_lo, steps_hi + 1, count)
+    return [dict(arrival=float(t[k]), n=int(ns[k]), rho=float(rhos[k]), T=float(ts[k]),
+                 steps=int(steps[k]), seed=seed + 100000 + k) for k in range(count)]
