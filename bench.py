@@ -1,0 +1,465 @@
+#!/usr/bin/env python
+"""Benchmark of the LJ MD hot path on GB300 (one JSON line on stdout, rank 0).
+
+Workload (default): the 64,000-particle Lennard-Jones fluid, rho 0.84, T 1.2,
+r_cut 2.5 sigma (energy-shifted), r_buff 0.4, dt 0.005, mixed precision (FP32 pair
+forces, FP64 positions/integration/reductions), seeded synthetic FCC+jitter input.
+A "step" is one velocity-Verlet time step of the whole path: integrate (+ the
+rebuild check), the conditional cell-list/neighbour-list rebuild, the pair force.
+
+Timing: W untimed warm-up steps, then exactly K steps, each bracketed by CUDA
+events on the system's stream, with a 256 MB write between steps so that every
+step starts with a cold L2 (the working set is smaller than the 129 MB L2).
+The force kernel of every timed step is bracketed by its own pair of events
+(recorded inside the step graph) for the roofline figure.  Clocks are sampled
+with nvidia-smi during the timed region.  The same protocol runs the plain FP64
+path for the "vs FP64 plain path" comparison, and an end-to-end loop through the
+public API with host buffers (upload state, run a chunk of steps, read energy
+and forces back) gives "e2e".
+
+--impl reference times the CPU oracle (FP64, O(N^2)) on this host's cores on a
+bounded sample of the same workload.  Under torchrun each rank runs its own
+replica (the path has no collective); value = all ranks' particle-steps / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-timesteps/sec and TPS (1 GB300) vs FP64 plain path; p50/p99 served latency"
+UNIT = "particle-steps/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ---------------------------------------------------------------------------
+# multi-rank plumbing (replicas only)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(world):
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend)
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def reduce_scalar(dist, x: float, op: str) -> float:
+    """max or sum of a float over ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3][k].lower() == "active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def make_workload(name: str, rank: int):
+    from paper_1308_5587_gb300 import workloads as wl
+    seed = wl.BASE_SEED + rank
+    if name == "lj64k":
+        return wl.lj_64k(seed), "mixed", 100, \
+            "lj_fluid N=64000 rho=0.84 T=1.2 rc=2.5 shifted rbuff=0.4 dt=0.005"
+    if name == "ka1m":
+        return wl.ka_1m(seed), "mixed", 100, \
+            "kob_andersen_80_20 N=1000000 rho=1.2 T=1.0 rc=2.5sigma_ij rbuff=0.3 dt=0.005 sort=100"
+    if name == "plain4k":
+        return wl.plain_fp64_4k(seed), "fp64", 0, \
+            "lj_fluid N=4000 rho=0.84 T=1.2 rc=2.5 shifted rbuff=0.4 dt=0.005 fp64"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_force.cu", "gbmd_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1308_5587_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, precision: str):
+    """dram bytes per force launch from a committed ncu summary, if the kernel is unchanged."""
+    p = os.path.join(ROOT, "profiles", "force_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    e = d.get(f"{workload}:{precision}")
+    if not e or e.get("kernel_sha") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def timed_steps(torch, s, K: int, W: int, flush, stream, dist):
+    """W warm-up steps, then K steps each bracketed by events; returns per-step and
+    per-force-kernel milliseconds and the number of library kernels executed."""
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    for e4 in ev:                    # torch creates the CUDA events at the first record
+        for e in e4:
+            e.record(stream)
+    torch.cuda.synchronize()
+    s.set_force_events(ev[0][1], ev[0][2])   # step graph built with the event nodes
+    for _ in range(W):
+        if flush is not None:
+            flush.zero_()
+        s.step(1)
+    s.sync()
+    barrier(dist)
+    torch.cuda.synchronize()
+    l0 = s.info()["kernel_launches"]
+    for k in range(K):
+        if flush is not None:
+            flush.zero_()
+        s.set_force_events(ev[k][1], ev[k][2])
+        ev[k][0].record(stream)
+        s.step(1)
+        ev[k][3].record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    s.sync()
+    l1 = s.info()["kernel_launches"]
+    s.set_force_events(None, None)
+    step_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
+    force_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
+    return step_ms, force_ms, l1 - l0
+
+
+def e2e_loop(torch, w, precision, sort_period, stream, dev, chunk: int, iters: int):
+    """Public-API loop with host buffers: upload (pinned) state -> `chunk` steps ->
+    read energy and forces back; wall-clock per particle-step."""
+    from paper_1308_5587_gb300 import gbmd
+    n = w.n
+    s = gbmd.System.from_workload(w, precision=precision, sort_period=sort_period,
+                                  stream=stream, cuda_device=dev)
+    pos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    vel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    img = torch.empty((n, 3), dtype=torch.int32, pin_memory=True).numpy()
+    frc = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pos[:] = w.pos
+    vel[:] = w.vel
+    img[:] = 0
+    for _ in range(2):   # warm-up
+        s.set_state(pos, vel, img, 0)
+        s.step(chunk)
+        s.thermo()
+        s.forces(out=frc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        s.set_state(pos, vel, img, 0)
+        s.step(chunk)
+        th = s.thermo()
+        s.forces(out=frc)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    assert math.isfinite(th["pe"])
+    return n * chunk * iters / dt, (pos.nbytes + vel.nbytes + img.nbytes) / chunk, \
+        (frc.nbytes + 8 * 11) / chunk
+
+
+def cpu_baseline(w, world_rank):
+    """The oracle as it stands: one full O(N^2) force evaluation (the per-step cost
+    of its velocity Verlet; the integration itself is O(N)), on all host cores."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    p = w.pairs.as_dict()
+    n = w.n
+    if n <= 100_000:
+        t0 = time.perf_counter()
+        oracle.forces(w.pos, w.box, w.types, p)
+        dt = time.perf_counter() - t0
+        return {"value": n / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                "sample": f"one full O(N^2) force evaluation of all {n} particles "
+                          f"({dt:.2f} s); integration is O(N) and not counted"}
+    m = 512
+    idx = np.random.default_rng(0).choice(n, m, replace=False)
+    t0 = time.perf_counter()
+    oracle.forces_subset(w.pos, w.box, w.types, p, idx)
+    dt = time.perf_counter() - t0
+    return {"value": m / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"forces on {m} sampled particles against all {n} ({dt:.2f} s), "
+                      "scaled per particle-step"}
+
+
+def gpu_arm(args):
+    import torch
+    from paper_1308_5587_gb300 import _build, gbmd
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world)
+    _build.build()
+    stream = torch.cuda.current_stream()
+    w, precision, sort_period, wdesc = make_workload(args.workload, rank)
+    n = w.n
+    flush = None
+    if args.workload != "ka1m":     # working set < L2: write 256 MB between steps
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    s = gbmd.System.from_workload(w, precision=precision, sort_period=sort_period,
+                                  stream=stream.cuda_stream, cuda_device=local)
+    if args.autotune:
+        s.autotune(os.path.join(ROOT, "_work", "tune_cache.txt") if os.path.isdir(
+            os.path.join(ROOT, "_work")) else None)
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, force_ms, launches = timed_steps(torch, s, args.steps, args.warmup, flush,
+                                              stream, dist)
+    clk = clocks.stop()
+    info = s.info()
+    th = s.thermo()
+    s.close()
+    assert math.isfinite(th["pe"]), "non-finite energy"
+
+    t_local = float(step_ms.sum()) / 1e3
+    t_max = reduce_scalar(dist, t_local, "max")
+    units = reduce_scalar(dist, n * args.steps, "sum")
+    value = units / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+
+    # roofline of the dominant kernel (pair force): algorithmic bytes per launch
+    nbar = info["neighbors_total"] / n
+    f_bytes = 16 if precision == "mixed" else 32
+    pos_bytes = 16 if precision == "mixed" else 32
+    alg_bytes = n * (pos_bytes + 4 + 4 * nbar + f_bytes)
+    peak, peak_kind = measured_peaks()
+    f_mean = float(force_ms.mean())
+    achieved = alg_bytes / (f_mean * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": recorded_traffic(args.workload, precision),
+                "kernel": f"k_force<{precision}> tpp={info['threads_per_particle']} "
+                          f"block={info['force_block']}",
+                "alg_bytes_per_launch": int(alg_bytes), "mean_neighbors": round(nbar, 2),
+                "force_ms_mean": round(f_mean, 5), "peak_kind": f"of {peak_kind}",
+                "force_share_of_step": round(f_mean / float(step_ms.mean()), 3)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 pair forces + f64 integration" if precision == "mixed" else "f64",
+           "data": "synthetic (seeded FCC + jitter, Maxwell-Boltzmann; no dataset)",
+           "config": {"workload": wdesc, "n": n, "precision": precision,
+                      "parallelism": f"replicas x{world}" if world > 1 else "single system",
+                      "l2": "flushed between steps (256 MB write)" if flush is not None
+                      else "inputs larger than L2 (nlist > 129 MB)",
+                      "timed_iteration": "one MD step (one single-step CUDA graph)",
+                      "threads_per_particle": info["threads_per_particle"],
+                      "force_block": info["force_block"], "nlist_capacity": info["nlist_capacity"],
+                      "sort_period": sort_period},
+           "tps": args.steps / t_max, "roofline": roofline, "clocks": clk,
+           "gpu_launches": int(launches),
+           "rebuilds_per_step": None}
+    out["rebuilds_per_step"] = round(info["n_rebuilds"] / max(info["step"], 1), 4)
+
+    # plain FP64 path on the same workload, same protocol
+    if not args.no_fp64 and precision == "mixed" and args.workload == "lj64k":
+        s64 = gbmd.System.from_workload(w, precision="fp64", sort_period=sort_period,
+                                        stream=stream.cuda_stream, cuda_device=local)
+        k64 = max(20, args.steps // 20)
+        st64, f64, _ = timed_steps(torch, s64, k64, max(3, args.warmup // 20), flush, stream, dist)
+        s64.close()
+        t64 = reduce_scalar(dist, float(st64.sum()) / 1e3, "max")
+        v64 = reduce_scalar(dist, n * k64, "sum") / t64
+        out["fp64_plain"] = {"value": v64, "unit": UNIT, "steps": k64,
+                             "ms_per_step": 1e3 * t64 / k64,
+                             "force_ms_mean": round(float(f64.mean()), 4),
+                             "mixed_over_fp64": round(value / v64, 2)}
+
+    # end to end through the public API with host buffers
+    chunk = 100
+    iters = max(3, min(30, args.steps // chunk))
+    e2e_v, h2d, d2h = e2e_loop(torch, w, precision, sort_period, stream.cuda_stream, local, chunk,
+                               iters)
+    e2e_v = reduce_scalar(dist, e2e_v, "sum")
+    out["e2e"] = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                  "d2h_bytes_per_step": int(d2h),
+                  "loop": f"{iters} x (set_state from pinned host -> {chunk} steps -> "
+                          "thermo + forces to pinned host)"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    w, precision, sort_period, wdesc = make_workload(args.workload, 0)
+    p = w.pairs.as_dict()
+    n = w.n
+    rng = np.random.default_rng(1)
+    # size each step's sample so that the whole run takes about two minutes
+    probe = rng.choice(n, 32, replace=False)
+    t0 = time.perf_counter()
+    oracle.forces_subset(w.pos, w.box, w.types, p, probe)
+    per_particle = (time.perf_counter() - t0) / 32
+    budget = 100.0 / max(args.steps + args.warmup, 1)
+    m = int(min(n, max(8, budget / max(per_particle, 1e-9))))
+    pos = w.pos.copy()
+    vel = w.vel.copy()
+    h = 0.5 * w.dt / w.mass
+
+    def one_step(k):
+        idx = rng.choice(n, m, replace=False)
+        F, _, _ = oracle.forces_subset(pos, w.box, w.types, p, idx)
+        vel[idx] += h * F            # the sampled particles' kick; drift below
+        pos[idx] += w.dt * vel[idx]
+
+    for k in range(args.warmup):
+        one_step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        one_step(k)
+    dt = time.perf_counter() - t0
+    value = m * args.steps / dt
+    sample = (f"per step: forces on {m} random particles against all {n} "
+              f"(O(m N) of the O(N^2) step) + their kick/drift")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * dt / args.steps * (n / m), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded FCC + jitter, Maxwell-Boltzmann; no dataset)",
+           "config": {"workload": wdesc, "n": n, "precision": "fp64 (CPU oracle)",
+                      "parallelism": "host cores"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["gbmd", "reference"], default="gbmd")
+    ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k"], default="lj64k")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

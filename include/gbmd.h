@@ -1,0 +1,254 @@
+/*
+ * gbmd.h -- C ABI of libgbmd, a GB300 (sm_103a) Lennard-Jones molecular-dynamics
+ * hot path: cell list, Verlet neighbour list with skin, LJ pair force and a fused
+ * velocity-Verlet NVE step, for one system or for many systems stepped together.
+ *
+ * The calls follow the HOOMD-blue paper's statement of the problem:
+ *   - a system is particles with positions and types in a periodic box
+ *     (Section 3.1, Listing 1: init.create_lattice);
+ *   - forces come from md.pair.lj(r_cut) with per type-pair epsilon and sigma
+ *     (Listing 1, pair_coeff.set), gathered from a cell-based neighbour list
+ *     (md.nlist.cell);
+ *   - md.integrate.mode_standard(dt) advances it; run(n) steps it n times
+ *     (Listing 1; NVE is among the ensembles of Section 3.1);
+ *   - results are force, energy and virial (Section 7.1).
+ * The paper gives no equations; the library computes:
+ *   V(r) = 4 eps[(sigma/r)^12 - (sigma/r)^6] - V_LJ(r_cut) for r < r_cut, else 0;
+ *   F_ij = 24 eps [2 (sigma/r)^12 - (sigma/r)^6] / r^2 * d_ij, d_ij = x_i - x_j
+ *   (minimum image); U = sum_{i<j} V; W_ab = sum_{i<j} d_ij,a F_ij,b;
+ *   K = 1/2 m sum v^2; T = 2K/(3N-3); P = (N T + tr W / 3) / V;
+ *   velocity Verlet: v += dt/(2m) F; x += dt v; wrap; F = F(x); v += dt/(2m) F.
+ * The neighbour list holds every pair with r < r_cut,ij + r_buff at its last
+ * build and is rebuilt when some particle has moved more than r_buff/2 since.
+ *
+ * Conventions for every call:
+ *   - Host arrays are row-major N x 3 (x, y, z per particle) in TAG order, the
+ *     order of the arrays given at creation; the library may reorder particles
+ *     internally (Morton/cell order) but every output is in tag order.
+ *   - The caller keeps ownership of every array it passes; the library copies
+ *     what it needs.  Output arrays are caller-allocated.
+ *   - Positions may be given in any periodic image; the library wraps them into
+ *     the centred box [-L/2, L/2) and keeps integer image counts.
+ *   - Return value: GBMD_OK (0) or a negative gbmd_status.  The library never
+ *     aborts the process and never traps on the device; device-side faults
+ *     (neighbour-list overflow, non-finite coordinates) are recorded in device
+ *     memory and reported by the next call that synchronises.  On error,
+ *     gbmd_last_error() returns a message for the calling thread.
+ *   - Asynchrony: gbmd_step / gbmd_batch_step only enqueue work on the system's
+ *     CUDA stream.  Every gbmd_get_* call synchronises that stream first.
+ */
+#ifndef GBMD_H
+#define GBMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBMD_ABI_VERSION 1
+#define GBMD_MAX_TYPES 4
+
+typedef enum gbmd_status {
+    GBMD_OK = 0,
+    GBMD_ERR_BAD_ARG = -1,          /* invalid argument (null pointer, size, parameter) */
+    GBMD_ERR_BOX_TOO_SMALL = -2,    /* some box edge < 2 (r_cut,max + r_buff) */
+    GBMD_ERR_OOM = -3,              /* device allocation failed */
+    GBMD_ERR_NLIST_OVERFLOW = -4,   /* neighbour list overflow that could not be recovered */
+    GBMD_ERR_NONFINITE = -5,        /* a coordinate became NaN/Inf, or moved > L/2 in a step */
+    GBMD_ERR_CUDA = -6,             /* a CUDA runtime call failed */
+    GBMD_ERR_TIMEOUT = -7,          /* a bounded wait ran out */
+    GBMD_ERR_STATE = -8,            /* call not valid in the current state (e.g. in a batch) */
+    GBMD_ERR_NO_DEVICE = -9         /* no usable CUDA device */
+} gbmd_status;
+
+typedef enum gbmd_precision {
+    GBMD_FP64 = 0,   /* every step in FP64 */
+    GBMD_MIXED = 1   /* FP32 pair forces and sums; FP64 positions, wrap, integration, reductions */
+} gbmd_precision;
+
+/* System description.  All pointers are read during gbmd_create* only. */
+typedef struct gbmd_desc {
+    int64_t n;                  /* number of particles, >= 1 */
+    double box[3];              /* orthorhombic box edges Lx, Ly, Lz (> 0) */
+    const double *pos;          /* n x 3 positions (any image) */
+    const double *vel;          /* n x 3 velocities */
+    const int32_t *type;        /* n type ids in [0, ntypes); NULL = all type 0 */
+    const int32_t *image;       /* n x 3 initial image counts; NULL = all 0 */
+    int32_t ntypes;             /* 1 .. GBMD_MAX_TYPES */
+    const double *eps;          /* ntypes x ntypes, symmetric, > 0 */
+    const double *sigma;        /* ntypes x ntypes, symmetric, > 0 */
+    const double *rcut;         /* ntypes x ntypes, symmetric, > 0 (r_cut per pair) */
+    double r_buff;              /* neighbour-list skin, >= 0 */
+    double dt;                  /* time step, > 0 */
+    double mass;                /* particle mass, > 0 */
+    int32_t precision;          /* gbmd_precision */
+    int32_t sort_period;        /* re-sort particles into Morton cell order at the first
+                                   rebuild at least this many steps after the last sort;
+                                   0 = sort only when the system is created */
+    int32_t nlist_capacity;     /* neighbours per particle to reserve; 0 = from density */
+    int32_t threads_per_particle; /* 0 = default (8); else 4, 8, 16 or 32 */
+    void *stream;               /* cudaStream_t to run on; NULL = the legacy default stream */
+    int32_t device;             /* CUDA device ordinal; -1 = the calling thread's current
+                                   device.  Every later call on the system uses it. */
+} gbmd_desc;
+
+/* Thermodynamic quantities of one system at its current step (FP64). */
+typedef struct gbmd_thermo {
+    int64_t step;
+    double pe;          /* U = sum_{i<j} V(r_ij) */
+    double ke;          /* K = 1/2 m sum v^2 at full-step velocities */
+    double temperature; /* 2K / (3N - 3) */
+    double pressure;    /* (N T + tr W / 3) / V */
+    double virial[6];   /* W: xx, xy, xz, yy, yz, zz */
+    double w;           /* tr W */
+    int64_t n_rebuilds; /* neighbour-list builds since creation */
+} gbmd_thermo;
+
+/* Configuration and counters of one system, for diagnostics and benchmarks. */
+typedef struct gbmd_info {
+    int64_t n;
+    int32_t precision;
+    int32_t ntypes;
+    int32_t cells[3];             /* cells per axis of the cell list */
+    int32_t nlist_capacity;       /* current neighbours-per-particle capacity */
+    int32_t threads_per_particle; /* lanes cooperating on one particle in the force kernel */
+    int32_t force_block;          /* threads per block of the force kernel */
+    int64_t step;
+    int64_t n_rebuilds;
+    int64_t n_sorts;
+    int64_t kernel_launches;      /* kernels of this library executed for this system
+                                     (counted on the device) */
+    int64_t neighbors_total;      /* sum of neighbour counts at the last build */
+    int64_t footprint_bytes;      /* device memory held */
+} gbmd_info;
+
+typedef struct gbmd_system gbmd_system;
+typedef struct gbmd_batch gbmd_batch;
+
+/* ---- single system ---------------------------------------------------------- */
+
+/* Create a system from HOST arrays: uploads, wraps, builds the cell and
+ * neighbour lists and computes the initial forces.  *out receives the handle.
+ * Errors: BAD_ARG, BOX_TOO_SMALL, OOM, CUDA, NO_DEVICE. */
+int gbmd_create(const gbmd_desc *d, gbmd_system **out);
+
+/* As gbmd_create, but pos, vel, type and image are DEVICE pointers (same
+ * layout, e.g. from torch tensors); the library copies them on d->stream. */
+int gbmd_create_device(const gbmd_desc *d, gbmd_system **out);
+
+/* Free every device and host resource of the system (synchronises). */
+int gbmd_destroy(gbmd_system *s);
+
+/* Enqueue nsteps velocity-Verlet steps (Listing 1's run(n)) on the system's
+ * stream and return without waiting.  nsteps >= 0.  Device-side errors surface
+ * at the next gbmd_sync / gbmd_get_*; a neighbour-list overflow is recovered
+ * there (capacity grown, the interrupted step redone, the remaining steps run).
+ * STATE if the system belongs to a batch. */
+int gbmd_step(gbmd_system *s, int64_t nsteps);
+
+/* Wait for the system's queued work, recover from a neighbour-list overflow if
+ * one happened, and report any other device-side error. */
+int gbmd_sync(gbmd_system *s);
+
+/* Forces on every particle at the current step, host n x 3, tag order. */
+int gbmd_get_forces(gbmd_system *s, double *out);
+
+/* Energy, virial, temperature and pressure at the current step. */
+int gbmd_get_thermo(gbmd_system *s, gbmd_thermo *out);
+
+/* Per-particle energy (n, half of every pair energy) and virial (n x 6, half of
+ * every pair virial), tag order; either pointer may be NULL. */
+int gbmd_get_per_particle(gbmd_system *s, double *energy, double *virial);
+
+/* Checkpoint: wrapped positions, full-step velocities, image counts (n x 3 each,
+ * any may be NULL) and the step counter (may be NULL). */
+int gbmd_get_state(gbmd_system *s, double *pos, double *vel, int32_t *image, int64_t *step);
+
+/* Resume: replace positions (any image), velocities and image counts (NULL image
+ * = zeros) and the step counter; rebuilds the lists and recomputes forces. */
+int gbmd_set_state(gbmd_system *s, const double *pos, const double *vel, const int32_t *image,
+                   int64_t step);
+
+/* Neighbour list of the last build, as tags: counts[n]; idx[n x cap] row-major,
+ * each row sorted ascending, unused entries -1.  BAD_ARG if some particle has
+ * more than cap neighbours (counts are still written). */
+int gbmd_get_neighbors(gbmd_system *s, int32_t *counts, int32_t *idx, int64_t cap);
+
+/* Configuration and counters. */
+int gbmd_get_info(gbmd_system *s, gbmd_info *out);
+
+/* Device bytes a system with this description would hold (for admission
+ * control); returns a negative gbmd_status for an invalid description. */
+int64_t gbmd_footprint_bytes(const gbmd_desc *d);
+
+/* Stop the system from advancing once its step counter reaches `step`
+ * (-1 = no limit).  Steps asked beyond the limit are skipped on the device. */
+int gbmd_set_step_limit(gbmd_system *s, int64_t step);
+
+/* Choose the force kernel's threads per particle and block size by timing the
+ * candidates on this system's current state; with a non-NULL cache_path the
+ * choice is read from / appended to that text file, keyed by precision, type
+ * count, size and density class. */
+int gbmd_autotune(gbmd_system *s, const char *cache_path);
+
+/* Set the force kernel's threads per particle (1,2,4,8,16,32) and block size
+ * (64..1024, a multiple of 32 and of tpp) explicitly. */
+int gbmd_set_tuning(gbmd_system *s, int32_t threads_per_particle, int32_t block);
+
+/* Bracket the force kernel of every subsequent single step (gbmd_step(s, 1)) with
+ * records of two CUDA events (cudaEvent_t, created by the caller with timing
+ * enabled), so the caller can time that kernel inside real steps; may be called
+ * between steps with new events (the step graph is updated, not rebuilt).
+ * NULL, NULL removes the records.  Multi-step calls are unaffected. */
+int gbmd_set_force_events(gbmd_system *s, void *ev_begin, void *ev_end);
+
+/* ---- many systems stepped together ------------------------------------------ */
+
+/* A batch steps all its systems with one launch per kernel per step (all systems
+ * share every launch) inside captured CUDA graphs.  Every member must have the
+ * batch's precision and device.  stream: cudaStream_t or NULL; device: ordinal
+ * or -1 for the calling thread's current device. */
+int gbmd_batch_create(int32_t precision, void *stream, int32_t device, gbmd_batch **out);
+
+/* Add a system (between steps only).  The system's own stream is replaced by the
+ * batch's while it is a member; gbmd_step on it returns STATE.  *slot receives a
+ * slot id for gbmd_batch_remove. */
+int gbmd_batch_add(gbmd_batch *b, gbmd_system *s, int32_t *slot);
+
+/* Remove the system in `slot` (between steps; synchronises).  The system stays
+ * valid and can be stepped alone or read out. */
+int gbmd_batch_remove(gbmd_batch *b, int32_t slot);
+
+/* Enqueue nsteps steps of every member (members past their step limit stay put). */
+int gbmd_batch_step(gbmd_batch *b, int64_t nsteps);
+
+/* Wait for the batch's work; recover overflowed members; report errors. */
+int gbmd_batch_sync(gbmd_batch *b);
+
+/* Autotune the batch's force kernel on its current members. */
+int gbmd_batch_autotune(gbmd_batch *b, const char *cache_path);
+
+/* Set the batch's force-kernel tuning explicitly (see gbmd_set_tuning). */
+int gbmd_batch_set_tuning(gbmd_batch *b, int32_t threads_per_particle, int32_t block);
+
+/* Number of members and total particles. */
+int gbmd_batch_info(gbmd_batch *b, int32_t *members, int64_t *particles,
+                    int64_t *kernel_launches);
+
+/* Destroy the batch; members stay valid and become stand-alone again. */
+int gbmd_batch_destroy(gbmd_batch *b);
+
+/* ---- misc ------------------------------------------------------------------- */
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *gbmd_last_error(void);
+
+/* GBMD_ABI_VERSION of the loaded library. */
+int gbmd_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBMD_H */

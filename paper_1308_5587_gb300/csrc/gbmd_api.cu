@@ -1,0 +1,1173 @@
+// gbmd_api.cu -- the C ABI of libgbmd (include/gbmd.h): systems, batches, CUDA
+// graphs with a device-decided rebuild, overflow recovery, readouts, autotuning.
+//
+// A "group" is the unit that is stepped: one system alone, or a batch of systems.
+// Its step is a CUDA graph per block of steps; per step:
+//   integrate (K6) -> IF(any system needs a rebuild) { bin -> scan -> scatter ->
+//   cellsort -> permute -> copyback -> nlist } -> force (K5).
+// The IF is a graph conditional node whose value the integrate kernel's last block
+// sets on the device, so a step never returns to the host.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "launch.cuh"
+
+using namespace gbmd;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? GBMD_ERR_OOM : GBMD_ERR_CUDA,          \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    }                                                                                    \
+  } while (0)
+
+#define RET(x)                 \
+  do {                         \
+    int r_ = (x);              \
+    if (r_ != GBMD_OK) return r_; \
+  } while (0)
+
+constexpr int STEPS_PER_GRAPH = 16;
+
+size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct Group;
+
+struct gbmd_system {
+  int device = 0;             // CUDA ordinal every call on this system uses
+  SysDev h{};                 // master descriptor (device pointers)
+  Flags* d_flags = nullptr;
+  cudaStream_t stream = nullptr;     // the caller's stream
+  std::vector<void*> allocs;
+  size_t footprint = 0;
+  Group* own = nullptr;       // the system alone
+  Group* batch = nullptr;
+  int batch_slot = -1;
+  long long target_step = 0;  // steps requested so far (absolute), host bookkeeping
+  long long step_limit = -1;
+  // staging for import/export (device)
+  double *d_pos = nullptr, *d_vel = nullptr, *d_frc = nullptr;
+  int *d_img = nullptr, *d_type = nullptr, *d_misc = nullptr;
+  double *d_ppu = nullptr, *d_ppw = nullptr;   // per-particle readout staging (lazy)
+  double* d_thermo = nullptr;
+};
+
+struct Group {
+  int device = 0;
+  std::vector<gbmd_system*> members;   // may contain nullptr (free slots of a batch)
+  bool is_batch = false;
+  int precision = GBMD_MIXED;
+  int multi = 0;
+  cudaStream_t stream = nullptr;
+  int tpp = 8, fblock = 256;
+  // device tables
+  SysDev* d_desc = nullptr;
+  Tile *d_tp = nullptr, *d_tf = nullptr, *d_tc = nullptr, *d_ts = nullptr;
+  int ntp = 0, ntf = 0, ntc = 0, nts = 0;
+  size_t cap_desc = 0, cap_tp = 0, cap_tf = 0, cap_tc = 0, cap_ts = 0, cap_part = 0;
+  double* d_partials = nullptr;
+  GroupCtl* d_ctl = nullptr;
+  cudaGraphExec_t exec_many = nullptr, exec_one = nullptr;
+  // optional event records around the force kernel of the single-step graph
+  cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+  cudaGraph_t graph_one = nullptr;                 // kept alive for node updates
+  cudaGraphNode_t node_ev_begin = nullptr, node_ev_end = nullptr;
+  bool layout_dirty = true;
+  bool graphs_dirty = true;
+  bool use_graphs = true;
+};
+
+namespace {
+
+// make `dev` current for this thread in this library's CUDA runtime
+int use_device(int dev) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) == cudaSuccess && cur == dev) return GBMD_OK;
+  CK(cudaSetDevice(dev));
+  return GBMD_OK;
+}
+
+std::vector<gbmd_system*> live(const Group* g) {
+  std::vector<gbmd_system*> v;
+  for (auto* s : g->members)
+    if (s) v.push_back(s);
+  return v;
+}
+
+template <typename T>
+int grow(T** p, size_t* cap, size_t need) {
+  if (*cap >= need && *p) return GBMD_OK;
+  if (*p) CK(cudaFree(*p));
+  *p = nullptr;
+  size_t n = std::max<size_t>(need, 1);
+  CK(cudaMalloc((void**)p, n * sizeof(T)));
+  *cap = n;
+  return GBMD_OK;
+}
+
+void destroy_graphs(Group* g) {
+  if (g->exec_many) cudaGraphExecDestroy(g->exec_many);
+  if (g->exec_one) cudaGraphExecDestroy(g->exec_one);
+  if (g->graph_one) cudaGraphDestroy(g->graph_one);
+  g->exec_many = g->exec_one = nullptr;
+  g->graph_one = nullptr;
+  g->node_ev_begin = g->node_ev_end = nullptr;
+  g->graphs_dirty = true;
+}
+
+// Rebuild descriptor copies and tile tables for the group's current members.
+int sync_layout(Group* g) {
+  if (!g->layout_dirty) return GBMD_OK;
+  std::vector<gbmd_system*> m = live(g);
+  std::vector<SysDev> desc;
+  std::vector<Tile> tp, tf, tc, ts;
+  const int per_f = g->fblock / g->tpp;
+  g->multi = 0;
+  for (size_t k = 0; k < m.size(); ++k) {
+    SysDev d = m[k]->h;
+    const int n = d.n;
+    for (int f = 0; f < n; f += TILE_P) tp.push_back({(int)k, f, std::min(TILE_P, n - f), 0});
+    d.tile_first_f = (int)tf.size();
+    for (int f = 0; f < n; f += per_f) tf.push_back({(int)k, f, std::min(per_f, n - f), 0});
+    d.tile_count_f = (int)tf.size() - d.tile_first_f;
+    for (int c = 0; c < d.ncells; c += CELLS_PER_TILE)
+      tc.push_back({(int)k, c, std::min(CELLS_PER_TILE, d.ncells - c), 0});
+    ts.push_back({(int)k, 0, 0, 0});
+    desc.push_back(d);
+    if (d.ntypes > 1) g->multi = 1;
+  }
+  RET(grow(&g->d_partials, &g->cap_part, 8 * std::max<size_t>(tf.size(), 1)));
+  for (auto& d : desc) d.partials = g->d_partials;
+  RET(grow(&g->d_desc, &g->cap_desc, desc.size()));
+  RET(grow(&g->d_tp, &g->cap_tp, tp.size()));
+  RET(grow(&g->d_tf, &g->cap_tf, tf.size()));
+  RET(grow(&g->d_tc, &g->cap_tc, tc.size()));
+  RET(grow(&g->d_ts, &g->cap_ts, ts.size()));
+  if (!g->d_ctl) {
+    CK(cudaMalloc(&g->d_ctl, sizeof(GroupCtl)));
+    CK(cudaMemsetAsync(g->d_ctl, 0, sizeof(GroupCtl), g->stream));
+  }
+  if (!desc.empty()) CK(cudaMemcpyAsync(g->d_desc, desc.data(), desc.size() * sizeof(SysDev), cudaMemcpyHostToDevice, g->stream));
+  if (!tp.empty()) CK(cudaMemcpyAsync(g->d_tp, tp.data(), tp.size() * sizeof(Tile), cudaMemcpyHostToDevice, g->stream));
+  if (!tf.empty()) CK(cudaMemcpyAsync(g->d_tf, tf.data(), tf.size() * sizeof(Tile), cudaMemcpyHostToDevice, g->stream));
+  if (!tc.empty()) CK(cudaMemcpyAsync(g->d_tc, tc.data(), tc.size() * sizeof(Tile), cudaMemcpyHostToDevice, g->stream));
+  if (!ts.empty()) CK(cudaMemcpyAsync(g->d_ts, ts.data(), ts.size() * sizeof(Tile), cudaMemcpyHostToDevice, g->stream));
+  CK(cudaStreamSynchronize(g->stream));   // host vectors die here
+  g->ntp = (int)tp.size();
+  g->ntf = (int)tf.size();
+  g->ntc = (int)tc.size();
+  g->nts = (int)ts.size();
+  g->layout_dirty = false;
+  destroy_graphs(g);
+  return GBMD_OK;
+}
+
+// update one member's descriptor in every group it belongs to (pointer/size change)
+int refresh_desc(gbmd_system* s) {
+  for (Group* g : {s->own, s->batch}) {
+    if (!g) continue;
+    g->layout_dirty = true;
+    RET(sync_layout(g));
+  }
+  return GBMD_OK;
+}
+
+std::vector<KernelCall> rebuild_calls(const Group* g) {
+  return {bin_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+          scan_call(g->d_desc, g->d_ts, g->nts, g->d_ctl),
+          scatter_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+          cellsort_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl),
+          permute_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+          copyback_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+          nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl)};
+}
+
+KernelCall step_force_call(const Group* g, int ev, int force_all) {
+  return force_call(g->precision, g->multi, ev, g->tpp, g->fblock, g->d_desc, g->d_tf, g->ntf,
+                    g->d_ctl, force_all);
+}
+
+int add_kernel(cudaGraph_t graph, const cudaGraphNode_t* dep, const KernelCall& k,
+               cudaGraphNode_t* out) {
+  cudaKernelNodeParams p{};
+  p.func = k.func;
+  p.gridDim = k.grid;
+  p.blockDim = k.block;
+  p.sharedMemBytes = (unsigned)k.smem;
+  void* a[10];
+  args_of(k, a);
+  p.kernelParams = a;
+  p.extra = nullptr;
+  CK(cudaGraphAddKernelNode(out, graph, dep, dep ? 1 : 0, &p));
+  return GBMD_OK;
+}
+
+int build_graph(Group* g, int nsteps, cudaGraphExec_t* exec) {
+  cudaGraph_t graph;
+  CK(cudaGraphCreate(&graph, 0));
+  const bool events = nsteps == 1 && g->ev_begin && g->ev_end;
+  cudaGraphNode_t prev = nullptr;
+  const int nsys = (int)live(g).size();
+  int rc = GBMD_OK;
+  for (int st = 0; st < nsteps && rc == GBMD_OK; ++st) {
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "conditional handle: %s", cudaGetErrorString(e)); break; }
+    cudaGraphNode_t n6, nc, n5;
+    rc = add_kernel(graph, prev ? &prev : nullptr,
+                    integrate_call(g->precision, g->d_desc, g->d_tp, g->ntp, g->d_ctl, nsys, h, 1), &n6);
+    if (rc) break;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&nc, graph, &n6, nullptr, 1, &cp);
+    if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "conditional node: %s", cudaGetErrorString(e)); break; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaGraphNode_t bprev = nullptr;
+    for (const KernelCall& k : rebuild_calls(g)) {
+      cudaGraphNode_t bn;
+      rc = add_kernel(body, bprev ? &bprev : nullptr, k, &bn);
+      if (rc) break;
+      bprev = bn;
+    }
+    if (rc) break;
+    cudaGraphNode_t before = nc;
+    if (events) {
+      e = cudaGraphAddEventRecordNode(&g->node_ev_begin, graph, &nc, 1, g->ev_begin);
+      if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "event node: %s", cudaGetErrorString(e)); break; }
+      before = g->node_ev_begin;
+    }
+    rc = add_kernel(graph, &before, step_force_call(g, 0, 0), &n5);
+    prev = n5;
+    if (rc == GBMD_OK && events) {
+      e = cudaGraphAddEventRecordNode(&g->node_ev_end, graph, &n5, 1, g->ev_end);
+      if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "event node: %s", cudaGetErrorString(e)); break; }
+      prev = g->node_ev_end;
+    }
+  }
+  if (rc == GBMD_OK) {
+    cudaError_t e = cudaGraphInstantiate(exec, graph, 0);
+    if (e != cudaSuccess) rc = fail(GBMD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  if (events && rc == GBMD_OK) g->graph_one = graph;   // node handles stay valid
+  else cudaGraphDestroy(graph);
+  return rc;
+}
+
+int ensure_graphs(Group* g) {
+  RET(sync_layout(g));
+  if (!g->graphs_dirty) return GBMD_OK;
+  RET(build_graph(g, STEPS_PER_GRAPH, &g->exec_many));
+  RET(build_graph(g, 1, &g->exec_one));
+  g->graphs_dirty = false;
+  return GBMD_OK;
+}
+
+// enqueue n steps of the group (graphs, or direct launches when graphs are off)
+int enqueue_steps(Group* g, long long n) {
+  if (n <= 0 || live(g).empty()) return GBMD_OK;
+  RET(sync_layout(g));
+  if (g->use_graphs) {
+    RET(ensure_graphs(g));
+    for (long long k = 0; k < n / STEPS_PER_GRAPH; ++k) CK(cudaGraphLaunch(g->exec_many, g->stream));
+    for (long long k = 0; k < n % STEPS_PER_GRAPH; ++k) CK(cudaGraphLaunch(g->exec_one, g->stream));
+    return GBMD_OK;
+  }
+  const int nsys = (int)live(g).size();
+  for (long long k = 0; k < n; ++k) {
+    CK(launch(integrate_call(g->precision, g->d_desc, g->d_tp, g->ntp, g->d_ctl, nsys, 0, 0), g->stream));
+    for (const KernelCall& c : rebuild_calls(g)) CK(launch(c, g->stream));
+    CK(launch(step_force_call(g, 0, 0), g->stream));
+  }
+  return GBMD_OK;
+}
+
+int read_flags(gbmd_system* s, Flags* f, cudaStream_t st) {
+  CK(cudaMemcpyAsync(f, s->d_flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return GBMD_OK;
+}
+
+int write_flags(gbmd_system* s, const Flags* f, cudaStream_t st) {
+  CK(cudaMemcpyAsync(s->d_flags, f, sizeof(Flags), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return GBMD_OK;
+}
+
+cudaStream_t cur_stream(gbmd_system* s) { return s->own->stream; }
+
+// rebuild lists (when flags->do_rebuild) + forces, outside any graph, for the system alone
+int rebuild_and_force(gbmd_system* s, int ev) {
+  Group* g = s->own;
+  RET(sync_layout(g));
+  for (const KernelCall& c : rebuild_calls(g)) CK(launch(c, g->stream));
+  CK(launch(step_force_call(g, ev, 1), g->stream));
+  return GBMD_OK;
+}
+
+int dalloc(gbmd_system* s, void** p, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 16);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return fail(GBMD_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  s->allocs.push_back(*p);
+  s->footprint += bytes;
+  return GBMD_OK;
+}
+
+// Grow the neighbour list to hold `need` neighbours per particle.
+int grow_nlist(gbmd_system* s, int need) {
+  const int cap = (int)round_up((size_t)need + need / 4 + 8, 8);
+  CK(cudaStreamSynchronize(cur_stream(s)));
+  auto it = std::find(s->allocs.begin(), s->allocs.end(), (void*)s->h.nl);
+  if (it != s->allocs.end()) {
+    s->allocs.erase(it);
+    s->footprint -= (size_t)s->h.n * s->h.cap * sizeof(int);
+  }
+  CK(cudaFree(s->h.nl));
+  s->h.nl = nullptr;
+  RET(dalloc(s, (void**)&s->h.nl, (size_t)s->h.n * cap * sizeof(int)));
+  s->h.cap = cap;
+  return refresh_desc(s);
+}
+
+// Wait for the system's work; recover from overflow; run what remains of its steps.
+int sync_system(gbmd_system* s) {
+  cudaStream_t st = cur_stream(s);
+  for (int round = 0; round < 64; ++round) {
+    CK(cudaStreamSynchronize(st));
+    Flags f;
+    RET(read_flags(s, &f, st));
+    if (f.error == DEV_NONFINITE)
+      return fail(GBMD_ERR_NONFINITE, "non-finite coordinate or a particle moved more than L/2 in one step (step %lld)", f.step);
+    if (f.error == DEV_OVERFLOW) {
+      RET(grow_nlist(s, std::max(f.overflow_need, s->h.cap + 1)));
+      f.error = 0;
+      f.overflow_need = 0;
+      f.do_rebuild = 1;
+      RET(write_flags(s, &f, st));
+      RET(rebuild_and_force(s, 0));   // finishes the interrupted step
+      continue;
+    }
+    if (f.error) return fail(GBMD_ERR_CUDA, "unknown device error %d", f.error);
+    long long want = s->target_step;
+    if (s->step_limit >= 0) want = std::min(want, s->step_limit);
+    if (f.step < want) {
+      RET(enqueue_steps(s->own, want - f.step));
+      continue;
+    }
+    return GBMD_OK;
+  }
+  return fail(GBMD_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+}
+
+int validate(const gbmd_desc* d, bool device) {
+  if (!d) return fail(GBMD_ERR_BAD_ARG, "desc is NULL");
+  if (d->n < 1 || d->n > (1LL << 30)) return fail(GBMD_ERR_BAD_ARG, "n must be in [1, 2^30], got %lld", (long long)d->n);
+  if (!d->pos || !d->vel) return fail(GBMD_ERR_BAD_ARG, "pos and vel must not be NULL");
+  if (d->ntypes < 1 || d->ntypes > GBMD_MAX_TYPES) return fail(GBMD_ERR_BAD_ARG, "ntypes must be in [1, %d]", GBMD_MAX_TYPES);
+  if (!d->eps || !d->sigma || !d->rcut) return fail(GBMD_ERR_BAD_ARG, "eps, sigma and rcut must not be NULL");
+  for (int a = 0; a < 3; ++a)
+    if (!(d->box[a] > 0) || !std::isfinite(d->box[a])) return fail(GBMD_ERR_BAD_ARG, "box edges must be positive and finite");
+  if (!(d->dt > 0) || !(d->mass > 0) || !(d->r_buff >= 0) || !std::isfinite(d->dt) || !std::isfinite(d->r_buff))
+    return fail(GBMD_ERR_BAD_ARG, "need dt > 0, mass > 0, r_buff >= 0");
+  if (d->precision != GBMD_FP64 && d->precision != GBMD_MIXED) return fail(GBMD_ERR_BAD_ARG, "precision must be GBMD_FP64 or GBMD_MIXED");
+  if (d->sort_period < 0 || d->nlist_capacity < 0) return fail(GBMD_ERR_BAD_ARG, "sort_period and nlist_capacity must be >= 0");
+  if (d->threads_per_particle != 0 && !tpp_supported(d->threads_per_particle))
+    return fail(GBMD_ERR_BAD_ARG, "threads_per_particle must be 0, 4, 8, 16 or 32");
+  const int nt = d->ntypes;
+  double rmax = 0;
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      const int p = a * nt + b, q = b * nt + a;
+      if (!(d->eps[p] > 0) || !(d->sigma[p] > 0) || !(d->rcut[p] > 0) || !std::isfinite(d->eps[p]) ||
+          !std::isfinite(d->sigma[p]) || !std::isfinite(d->rcut[p]))
+        return fail(GBMD_ERR_BAD_ARG, "pair parameters must be positive and finite");
+      if (d->eps[p] != d->eps[q] || d->sigma[p] != d->sigma[q] || d->rcut[p] != d->rcut[q])
+        return fail(GBMD_ERR_BAD_ARG, "pair parameter tables must be symmetric");
+      rmax = std::max(rmax, d->rcut[p]);
+    }
+  const double rl = rmax + d->r_buff;
+  for (int a = 0; a < 3; ++a)
+    if (d->box[a] < 2.0 * rl)
+      return fail(GBMD_ERR_BOX_TOO_SMALL, "box edge %d (%g) < 2 (r_cut,max + r_buff) = %g", a, d->box[a], 2 * rl);
+  if (!device) {
+    for (int64_t i = 0; i < 3 * d->n; ++i)
+      if (!std::isfinite(d->pos[i]) || !std::isfinite(d->vel[i])) return fail(GBMD_ERR_BAD_ARG, "non-finite position or velocity");
+    if (d->type)
+      for (int64_t i = 0; i < d->n; ++i)
+        if (d->type[i] < 0 || d->type[i] >= nt) return fail(GBMD_ERR_BAD_ARG, "type id out of range at %lld", (long long)i);
+  }
+  return GBMD_OK;
+}
+
+struct Geometry {
+  int nc[3];
+  int ncells;
+  int cap;
+  double rl_max;
+};
+
+Geometry geometry(const gbmd_desc* d) {
+  Geometry g;
+  const int nt = d->ntypes;
+  double rmax = 0;
+  for (int p = 0; p < nt * nt; ++p) rmax = std::max(rmax, d->rcut[p]);
+  g.rl_max = rmax + d->r_buff;
+  g.ncells = 1;
+  for (int a = 0; a < 3; ++a) {
+    int c = (int)std::floor(d->box[a] / (g.rl_max * (1.0 + 1e-6)));
+    g.nc[a] = std::min(std::max(c, 1), 1024);
+    g.ncells *= g.nc[a];
+  }
+  if (d->nlist_capacity > 0) {
+    g.cap = d->nlist_capacity;
+  } else {
+    const double rho = (double)d->n / (d->box[0] * d->box[1] * d->box[2]);
+    const double nexp = rho * 4.0 / 3.0 * M_PI * g.rl_max * g.rl_max * g.rl_max;
+    g.cap = (int)round_up((size_t)(nexp * 1.4 + 24), 8);
+    g.cap = std::min<int>(g.cap, (int)std::max<int64_t>(8, round_up((size_t)d->n, 8)));
+  }
+  return g;
+}
+
+uint32_t spread3(uint32_t v) {   // 10 bits -> every third bit
+  v &= 0x3ff;
+  v = (v | (v << 16)) & 0x030000FF;
+  v = (v | (v << 8)) & 0x0300F00F;
+  v = (v | (v << 4)) & 0x030C30C3;
+  v = (v | (v << 2)) & 0x09249249;
+  return v;
+}
+
+size_t footprint_of(const gbmd_desc* d, const Geometry& g) {
+  const size_t n = (size_t)d->n;
+  size_t b = 0;
+  b += n * (8 * 3 * 2);          // x, v
+  b += n * 4 * 3 + n * 4 * 3;    // img, rtag/tag/type
+  b += n * 16 * 2;               // q, q_build
+  b += n * 32;                   // p64
+  b += n * (d->precision == GBMD_FP64 ? 32 : 16);   // force
+  b += n * 4 + n * 4 * (size_t)g.cap;                // nn, nl
+  b += n * 4 * 3 + (size_t)(g.ncells + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;  // cells
+  b += n * (8 * 3 * 2 + 4 * 3 + 4 * 2 + 16);         // re-sort scratch
+  b += n * (8 * 3 * 3 + 4 * 3 + 4 * 2);              // import/export staging
+  b += 4096;
+  return b;
+}
+
+int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
+  if (!out) return fail(GBMD_ERR_BAD_ARG, "out is NULL");
+  *out = nullptr;
+  RET(validate(d, device));
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(GBMD_ERR_NO_DEVICE, "no CUDA device");
+  int dev = d->device;
+  if (dev < 0) CK(cudaGetDevice(&dev));
+  if (dev >= ndev) return fail(GBMD_ERR_BAD_ARG, "device %d does not exist (%d devices)", dev, ndev);
+  RET(use_device(dev));
+  const Geometry geo = geometry(d);
+  gbmd_system* s = new gbmd_system();
+  s->device = dev;
+  s->stream = (cudaStream_t)d->stream;
+  SysDev& h = s->h;
+  const int n = (int)d->n, nt = d->ntypes;
+  h.n = n;
+  h.ntypes = nt;
+  h.precision = d->precision;
+  h.sort_period = d->sort_period;
+  h.cap = geo.cap;
+  h.dt = d->dt;
+  h.mass = d->mass;
+  h.h = 0.5 * d->dt / d->mass;
+  h.ncells = geo.ncells;
+  for (int a = 0; a < 3; ++a) {
+    h.L[a] = d->box[a];
+    h.halfL[a] = 0.5 * d->box[a];
+    h.qscale[a] = 4294967296.0 / d->box[a];
+    h.fscale[a] = (float)(d->box[a] / 4294967296.0);
+    h.nc[a] = geo.nc[a];
+  }
+  const double hb = 0.5 * d->r_buff;
+  h.rbuff_half2 = (float)(hb * hb * (1.0 - 1e-5));
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      const int p = a * nt + b;
+      const double e = d->eps[p], sg = d->sigma[p], rc = d->rcut[p];
+      const double s6 = std::pow(sg, 6.0), s12 = s6 * s6;
+      const double c2 = sg * sg / (rc * rc), c6 = c2 * c2 * c2, c12 = c6 * c6;
+      const double rl = rc + d->r_buff;
+      PairD& pd = h.pd[p];
+      pd.lj1 = 48.0 * e * s12;
+      pd.lj2 = 24.0 * e * s6;
+      pd.rc2 = rc * rc;
+      pd.rl2 = rl * rl;
+      pd.c12 = 4.0 * e * s12;
+      pd.c6 = 4.0 * e * s6;
+      pd.shift = 4.0 * e * (c12 - c6);
+      PairF& pf = h.pf[p];
+      pf.lj1 = (float)pd.lj1;
+      pf.lj2 = (float)pd.lj2;
+      pf.rc2 = (float)pd.rc2;
+      pf.c12 = (float)pd.c12;
+      pf.c6 = (float)pd.c6;
+      pf.shift = (float)pd.shift;
+      pf.rl2 = (float)pd.rl2;
+    }
+  int rc = GBMD_OK;
+  auto A = [&](void** p, size_t bytes) {
+    if (rc == GBMD_OK) rc = dalloc(s, p, bytes);
+  };
+  const size_t N = (size_t)n;
+  A((void**)&h.x, N * 24); A((void**)&h.v, N * 24); A((void**)&h.img, N * 12);
+  A((void**)&h.type, N * 4); A((void**)&h.tag, N * 4); A((void**)&h.rtag, N * 4);
+  A((void**)&h.q, N * 16); A((void**)&h.q_build, N * 16); A((void**)&h.p64, N * 32);
+  if (d->precision == GBMD_FP64) A((void**)&h.f64, N * 32); else A((void**)&h.f32, N * 16);
+  A((void**)&h.nn, N * 4); A((void**)&h.nl, N * 4 * (size_t)geo.cap);
+  A((void**)&h.key, N * 4); A((void**)&h.members, N * 4); A((void**)&h.members_tmp, N * 4);
+  A((void**)&h.cell_cnt, (geo.ncells + 1) * 4); A((void**)&h.cell_start, (geo.ncells + 1) * 4);
+  A((void**)&h.cell_cursor, (geo.ncells + 1) * 4);
+  int *r2l = nullptr, *l2r = nullptr;
+  A((void**)&r2l, geo.ncells * 4); A((void**)&l2r, geo.ncells * 4);
+  h.rank2lin = r2l; h.lin2rank = l2r;
+  A((void**)&h.x_alt, N * 24); A((void**)&h.v_alt, N * 24); A((void**)&h.img_alt, N * 12);
+  A((void**)&h.type_alt, N * 4); A((void**)&h.tag_alt, N * 4); A((void**)&h.q_alt, N * 16);
+  A((void**)&h.thermo, 16 * 8);
+  A((void**)&s->d_flags, sizeof(Flags));
+  A((void**)&s->d_pos, N * 24); A((void**)&s->d_vel, N * 24); A((void**)&s->d_frc, N * 24);
+  A((void**)&s->d_img, N * 12); A((void**)&s->d_type, N * 4); A((void**)&s->d_misc, 64);
+  h.flags = s->d_flags;
+  s->d_thermo = h.thermo;
+  if (rc != GBMD_OK) { gbmd_destroy(s); return rc; }
+  cudaStream_t st = s->stream;
+  // Morton rank of every cell
+  {
+    std::vector<std::pair<uint32_t, int>> code(geo.ncells);
+    for (int z = 0; z < geo.nc[2]; ++z)
+      for (int y = 0; y < geo.nc[1]; ++y)
+        for (int x = 0; x < geo.nc[0]; ++x) {
+          const int lin = (z * geo.nc[1] + y) * geo.nc[0] + x;
+          code[lin] = {spread3(x) | (spread3(y) << 1) | (spread3(z) << 2), lin};
+        }
+    std::sort(code.begin(), code.end());
+    std::vector<int> rl(geo.ncells), lr(geo.ncells);
+    for (int r = 0; r < geo.ncells; ++r) {
+      rl[r] = code[r].second;
+      lr[code[r].second] = r;
+    }
+    cudaError_t e1 = cudaMemcpyAsync(r2l, rl.data(), geo.ncells * 4, cudaMemcpyHostToDevice, st);
+    cudaError_t e2 = cudaMemcpyAsync(l2r, lr.data(), geo.ncells * 4, cudaMemcpyHostToDevice, st);
+    cudaError_t e3 = cudaMemsetAsync(h.cell_cnt, 0, (geo.ncells + 1) * 4, st);
+    cudaError_t e5 = cudaMemsetAsync(s->d_flags, 0, sizeof(Flags), st);
+    cudaError_t e6 = cudaMemsetAsync(h.nn, 0, N * 4, st);
+    cudaError_t e4 = cudaStreamSynchronize(st);
+    if (e1 || e2 || e3 || e4 || e5 || e6) { gbmd_destroy(s); return fail(GBMD_ERR_CUDA, "uploading the cell tables failed"); }
+  }
+  // own group
+  s->own = new Group();
+  s->own->device = dev;
+  s->own->stream = st;
+  s->own->precision = d->precision;
+  s->own->members.push_back(s);
+  if (d->threads_per_particle) s->own->tpp = d->threads_per_particle;
+  if (const char* ev = getenv("GBMD_NO_GRAPHS")) s->own->use_graphs = ev[0] != '1';
+  *out = s;
+  return GBMD_OK;
+}
+
+// Upload positions/velocities/types/images (tag order, host or device memory),
+// then build the lists (with the initial Morton sort) and compute the forces.
+int load_state(gbmd_system* s, const double* pos, const double* vel, const int32_t* type,
+               const int32_t* image, bool device, long long step) {
+  cudaStream_t st = cur_stream(s);
+  const size_t N = (size_t)s->h.n;
+  const double *dp = pos, *dv = vel;
+  const int *dt = type, *di = image;
+  if (!device) {
+    CK(cudaMemcpyAsync(s->d_pos, pos, N * 24, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->d_vel, vel, N * 24, cudaMemcpyHostToDevice, st));
+    dp = s->d_pos;
+    dv = s->d_vel;
+    if (type) {
+      CK(cudaMemcpyAsync(s->d_type, type, N * 4, cudaMemcpyHostToDevice, st));
+      dt = s->d_type;
+    }
+    if (image) {
+      CK(cudaMemcpyAsync(s->d_img, image, N * 12, cudaMemcpyHostToDevice, st));
+      di = s->d_img;
+    }
+  }
+  Group* g = s->own;
+  RET(sync_layout(g));
+  CK(launch(import_call(g->d_desc, g->d_tp, g->ntp, dp, dv, dt, di), st));
+  Flags f{};
+  f.do_rebuild = 1;
+  f.do_sort = 1;
+  f.v_full = 1;
+  f.active = 1;
+  f.step = step;
+  f.step_limit = s->step_limit;
+  f.last_sort = step;
+  Flags old{};
+  CK(cudaMemcpyAsync(&old, s->d_flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (old.error == DEV_BADTYPE) return fail(GBMD_ERR_BAD_ARG, "type id out of range in the device type array");
+  f.n_rebuilds = old.n_rebuilds;
+  f.n_sorts = old.n_sorts + 1;
+  f.launches = old.launches;
+  RET(write_flags(s, &f, st));
+  s->target_step = step;
+  RET(rebuild_and_force(s, 0));
+  CK(cudaStreamSynchronize(st));
+  Flags after;
+  RET(read_flags(s, &after, st));
+  if (after.error == DEV_OVERFLOW) {
+    RET(grow_nlist(s, after.overflow_need));
+    after.error = 0;
+    after.overflow_need = 0;
+    after.do_rebuild = 1;
+    RET(write_flags(s, &after, st));
+    RET(rebuild_and_force(s, 0));
+    RET(read_flags(s, &after, st));
+    if (after.error) return fail(GBMD_ERR_NLIST_OVERFLOW, "neighbour list overflow at creation");
+  }
+  return GBMD_OK;
+}
+
+int thermo_impl(gbmd_system* s, double out[8]) {
+  Group* g = s->own;
+  RET(sync_layout(g));
+  cudaStream_t st = cur_stream(s);
+  CK(launch(step_force_call(g, 1, 1), st));
+  CK(launch(thermo_call(g->d_desc, g->d_ts, g->nts, g->d_ctl), st));
+  CK(cudaMemcpyAsync(out, s->d_thermo, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return GBMD_OK;
+}
+
+int export_impl(gbmd_system* s, double* pos, double* vel, int32_t* image, double* force,
+                double* pp_u, double* pp_w) {
+  Group* g = s->own;
+  RET(sync_layout(g));
+  cudaStream_t st = cur_stream(s);
+  const size_t N = (size_t)s->h.n;
+  if ((pp_u || pp_w) && !s->d_ppw) return fail(GBMD_ERR_STATE, "per-particle arrays not allocated");
+  CK(launch(export_call(g->d_desc, g->d_tp, g->ntp, pos ? s->d_pos : nullptr,
+                        vel ? s->d_vel : nullptr, image ? s->d_img : nullptr,
+                        force ? s->d_frc : nullptr, pp_u ? s->d_ppu : nullptr,
+                        pp_w ? s->d_ppw : nullptr), st));
+  if (pos) CK(cudaMemcpyAsync(pos, s->d_pos, N * 24, cudaMemcpyDeviceToHost, st));
+  if (vel) CK(cudaMemcpyAsync(vel, s->d_vel, N * 24, cudaMemcpyDeviceToHost, st));
+  if (image) CK(cudaMemcpyAsync(image, s->d_img, N * 12, cudaMemcpyDeviceToHost, st));
+  if (force) CK(cudaMemcpyAsync(force, s->d_frc, N * 24, cudaMemcpyDeviceToHost, st));
+  if (pp_u) CK(cudaMemcpyAsync(pp_u, s->d_ppu, N * 8, cudaMemcpyDeviceToHost, st));
+  if (pp_w) CK(cudaMemcpyAsync(pp_w, s->d_ppw, N * 48, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return GBMD_OK;
+}
+
+int time_force(Group* g, float* ms) {
+  RET(sync_layout(g));
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  for (int k = 0; k < 2; ++k) CK(launch(step_force_call(g, 0, 1), g->stream));
+  CK(cudaEventRecord(a, g->stream));
+  const int reps = 5;
+  for (int k = 0; k < reps; ++k) CK(launch(step_force_call(g, 0, 1), g->stream));
+  CK(cudaEventRecord(b, g->stream));
+  CK(cudaEventSynchronize(b));
+  float t = 0;
+  CK(cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t / reps;
+  return GBMD_OK;
+}
+
+std::string tune_key(const Group* g) {
+  std::vector<gbmd_system*> m = live(g);
+  long long np = 0;
+  double vol = 0;
+  for (auto* s : m) {
+    np += s->h.n;
+    vol += s->h.L[0] * s->h.L[1] * s->h.L[2];
+  }
+  const int lg = np > 0 ? (int)std::floor(std::log2((double)np)) : 0;
+  const int rho10 = vol > 0 ? (int)std::lround(10.0 * np / vol) : 0;
+  char buf[512];
+  cudaDeviceProp p{};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&p, dev);
+  snprintf(buf, sizeof(buf), "%s|prec=%d|multi=%d|members=%d|log2n=%d|rho10=%d", p.name,
+           g->precision, g->multi, (int)m.size(), lg, rho10);
+  for (char* c = buf; *c; ++c)
+    if (*c == ' ') *c = '_';
+  return buf;
+}
+
+int set_tuning(Group* g, int tpp, int block) {
+  if (!tpp_supported(tpp) || block < 64 || block > 1024 || block % 32 || block % tpp)
+    return fail(GBMD_ERR_BAD_ARG, "bad tuning tpp=%d block=%d", tpp, block);
+  if (g->tpp == tpp && g->fblock == block) return GBMD_OK;
+  g->tpp = tpp;
+  g->fblock = block;
+  g->layout_dirty = true;
+  return sync_layout(g);
+}
+
+int autotune_group(Group* g, const char* cache) {
+  RET(sync_layout(g));
+  const std::string key = tune_key(g);
+  if (cache) {
+    std::ifstream in(cache);
+    std::string line;
+    int bt = 0, bb = 0;
+    while (std::getline(in, line)) {
+      std::istringstream ls(line);
+      std::string k;
+      int t, b;
+      if (ls >> k >> t >> b && k == key) { bt = t; bb = b; }
+    }
+    if (bt) return set_tuning(g, bt, bb);
+  }
+  int best_t = g->tpp, best_b = g->fblock;
+  float best = 1e30f;
+  for (int tpp : {4, 8, 16, 32})
+    for (int block : {128, 256, 512}) {
+      RET(set_tuning(g, tpp, block));
+      float ms;
+      RET(time_force(g, &ms));
+      if (ms < best) { best = ms; best_t = tpp; best_b = block; }
+    }
+  RET(set_tuning(g, best_t, best_b));
+  if (cache) {
+    std::ofstream o(cache, std::ios::app);
+    o << key << " " << best_t << " " << best_b << "\n";
+  }
+  return GBMD_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* gbmd_last_error(void) { return g_err.c_str(); }
+
+int gbmd_abi_version(void) { return GBMD_ABI_VERSION; }
+
+int gbmd_create(const gbmd_desc* d, gbmd_system** out) {
+  RET(create_impl(d, out, false));
+  int rc = load_state(*out, d->pos, d->vel, d->type, d->image, false, 0);
+  if (rc != GBMD_OK) {
+    std::string msg = g_err;
+    gbmd_destroy(*out);
+    *out = nullptr;
+    g_err = msg;
+  }
+  return rc;
+}
+
+int gbmd_create_device(const gbmd_desc* d, gbmd_system** out) {
+  RET(create_impl(d, out, true));
+  int rc = load_state(*out, d->pos, d->vel, d->type, d->image, true, 0);
+  if (rc != GBMD_OK) {
+    std::string msg = g_err;
+    gbmd_destroy(*out);
+    *out = nullptr;
+    g_err = msg;
+  }
+  return rc;
+}
+
+int gbmd_destroy(gbmd_system* s) {
+  if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
+  use_device(s->device);
+  if (s->batch) {
+    Group* b = s->batch;
+    for (auto& m : b->members)
+      if (m == s) m = nullptr;
+    b->layout_dirty = true;
+    s->batch = nullptr;
+  }
+  if (s->own) cudaStreamSynchronize(s->own->stream);
+  for (void* p : s->allocs) cudaFree(p);
+  if (s->own) {
+    Group* g = s->own;
+    destroy_graphs(g);
+    cudaFree(g->d_desc); cudaFree(g->d_tp); cudaFree(g->d_tf); cudaFree(g->d_tc);
+    cudaFree(g->d_ts); cudaFree(g->d_partials); cudaFree(g->d_ctl);
+    delete g;
+  }
+  delete s;
+  return GBMD_OK;
+}
+
+int gbmd_step(gbmd_system* s, int64_t nsteps) {
+  if (!s || nsteps < 0) return fail(GBMD_ERR_BAD_ARG, "bad system or nsteps");
+  RET(use_device(s->device));
+  if (s->batch) return fail(GBMD_ERR_STATE, "system belongs to a batch; use gbmd_batch_step");
+  s->target_step += nsteps;
+  return enqueue_steps(s->own, nsteps);
+}
+
+int gbmd_sync(gbmd_system* s) {
+  if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
+  RET(use_device(s->device));
+  return sync_system(s);
+}
+
+int gbmd_get_forces(gbmd_system* s, double* out) {
+  if (!s || !out) return fail(GBMD_ERR_BAD_ARG, "NULL argument");
+  RET(use_device(s->device));
+  RET(sync_system(s));
+  return export_impl(s, nullptr, nullptr, nullptr, out, nullptr, nullptr);
+}
+
+int gbmd_get_thermo(gbmd_system* s, gbmd_thermo* out) {
+  if (!s || !out) return fail(GBMD_ERR_BAD_ARG, "NULL argument");
+  RET(use_device(s->device));
+  RET(sync_system(s));
+  double t[8];
+  RET(thermo_impl(s, t));
+  Flags f;
+  RET(read_flags(s, &f, cur_stream(s)));
+  const double n = (double)s->h.n;
+  const double vol = s->h.L[0] * s->h.L[1] * s->h.L[2];
+  out->step = f.step;
+  out->pe = t[0];
+  out->ke = 0.5 * s->h.mass * t[1];
+  out->temperature = n > 1 ? 2.0 * out->ke / (3.0 * n - 3.0) : 0.0;
+  for (int c = 0; c < 6; ++c) out->virial[c] = t[2 + c];
+  out->w = t[2] + t[5] + t[7];
+  out->pressure = (n * out->temperature + out->w / 3.0) / vol;
+  out->n_rebuilds = f.n_rebuilds;
+  return GBMD_OK;
+}
+
+int gbmd_get_per_particle(gbmd_system* s, double* energy, double* virial) {
+  if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
+  RET(use_device(s->device));
+  RET(sync_system(s));
+  if (!s->h.pp_u) {
+    const size_t N = (size_t)s->h.n;
+    RET(dalloc(s, (void**)&s->h.pp_u, N * 8));
+    RET(dalloc(s, (void**)&s->h.pp_w, N * 48));
+    RET(dalloc(s, (void**)&s->d_ppu, N * 8));
+    RET(dalloc(s, (void**)&s->d_ppw, N * 48));
+    RET(refresh_desc(s));
+  }
+  double t[8];
+  RET(thermo_impl(s, t));   // the energy pass fills the per-particle arrays
+  return export_impl(s, nullptr, nullptr, nullptr, nullptr, energy, virial);
+}
+
+int gbmd_get_state(gbmd_system* s, double* pos, double* vel, int32_t* image, int64_t* step) {
+  if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
+  RET(use_device(s->device));
+  RET(sync_system(s));
+  RET(export_impl(s, pos, vel, image, nullptr, nullptr, nullptr));
+  if (step) {
+    Flags f;
+    RET(read_flags(s, &f, cur_stream(s)));
+    *step = f.step;
+  }
+  return GBMD_OK;
+}
+
+int gbmd_set_state(gbmd_system* s, const double* pos, const double* vel, const int32_t* image,
+                   int64_t step) {
+  if (!s || !pos || !vel || step < 0) return fail(GBMD_ERR_BAD_ARG, "bad argument");
+  RET(use_device(s->device));
+  if (s->batch) return fail(GBMD_ERR_STATE, "remove the system from its batch first");
+  RET(sync_system(s));
+  const size_t N = (size_t)s->h.n;
+  for (size_t i = 0; i < 3 * N; ++i)
+    if (!std::isfinite(pos[i]) || !std::isfinite(vel[i])) return fail(GBMD_ERR_BAD_ARG, "non-finite state");
+  // types in tag order, gathered from the internal arrays
+  std::vector<int> types(N), tags(N);
+  cudaStream_t st = cur_stream(s);
+  CK(cudaMemcpyAsync(types.data(), s->h.type, N * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(tags.data(), s->h.tag, N * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<int> by_tag(N);
+  for (size_t k = 0; k < N; ++k) by_tag[tags[k]] = types[k];
+  return load_state(s, pos, vel, by_tag.data(), image, false, step);
+}
+
+int gbmd_get_neighbors(gbmd_system* s, int32_t* counts, int32_t* idx, int64_t cap) {
+  if (!s || !counts || !idx || cap < 1 || cap > (1 << 20)) return fail(GBMD_ERR_BAD_ARG, "bad argument");
+  RET(use_device(s->device));
+  RET(sync_system(s));
+  Group* g = s->own;
+  RET(sync_layout(g));
+  cudaStream_t st = cur_stream(s);
+  const size_t N = (size_t)s->h.n;
+  int *dc = nullptr, *di = nullptr, *dflag = s->d_misc;
+  CK(cudaMalloc(&dc, N * 4));
+  cudaError_t e = cudaMalloc(&di, N * (size_t)cap * 4);
+  if (e != cudaSuccess) {
+    cudaFree(dc);
+    return fail(GBMD_ERR_OOM, "no room for the neighbour readout");
+  }
+  int too_many = 0;
+  int rc = GBMD_OK;
+  if (cudaMemsetAsync(dflag, 0, 4, st) != cudaSuccess ||
+      launch(nlist_export_call(g->d_desc, g->d_tp, g->ntp, dc, di, (int)cap, dflag), st) != cudaSuccess ||
+      cudaMemcpyAsync(counts, dc, N * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(idx, di, N * (size_t)cap * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&too_many, dflag, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    rc = fail(GBMD_ERR_CUDA, "neighbour readout failed");
+  cudaFree(dc);
+  cudaFree(di);
+  if (rc == GBMD_OK && too_many) rc = fail(GBMD_ERR_BAD_ARG, "some particle has more than cap neighbours");
+  return rc;
+}
+
+int gbmd_get_info(gbmd_system* s, gbmd_info* out) {
+  if (!s || !out) return fail(GBMD_ERR_BAD_ARG, "NULL argument");
+  RET(use_device(s->device));
+  RET(sync_system(s));
+  Flags f;
+  RET(read_flags(s, &f, cur_stream(s)));
+  Group* g = s->batch ? s->batch : s->own;
+  out->n = s->h.n;
+  out->precision = s->h.precision;
+  out->ntypes = s->h.ntypes;
+  for (int a = 0; a < 3; ++a) out->cells[a] = s->h.nc[a];
+  out->nlist_capacity = s->h.cap;
+  out->threads_per_particle = g->tpp;
+  out->force_block = g->fblock;
+  out->step = f.step;
+  out->n_rebuilds = f.n_rebuilds;
+  out->n_sorts = f.n_sorts;
+  out->kernel_launches = (int64_t)f.launches;
+  out->neighbors_total = (int64_t)f.nb_total;
+  out->footprint_bytes = (int64_t)s->footprint;
+  return GBMD_OK;
+}
+
+int64_t gbmd_footprint_bytes(const gbmd_desc* d) {
+  if (!d || d->n < 1 || d->ntypes < 1 || d->ntypes > GBMD_MAX_TYPES || !d->rcut)
+    return fail(GBMD_ERR_BAD_ARG, "bad description");
+  for (int a = 0; a < 3; ++a)
+    if (!(d->box[a] > 0)) return fail(GBMD_ERR_BAD_ARG, "bad box");
+  return (int64_t)footprint_of(d, geometry(d));
+}
+
+int gbmd_set_step_limit(gbmd_system* s, int64_t step) {
+  if (!s || step < -1) return fail(GBMD_ERR_BAD_ARG, "bad argument");
+  RET(use_device(s->device));
+  cudaStream_t st = cur_stream(s);
+  CK(cudaStreamSynchronize(st));
+  Flags f;
+  RET(read_flags(s, &f, st));
+  f.step_limit = step;
+  s->step_limit = step;
+  return write_flags(s, &f, st);
+}
+
+int gbmd_set_force_events(gbmd_system* s, void* ev_begin, void* ev_end) {
+  if (!s || (!ev_begin) != (!ev_end)) return fail(GBMD_ERR_BAD_ARG, "bad argument");
+  RET(use_device(s->device));
+  Group* g = s->batch ? s->batch : s->own;
+  cudaEvent_t b = (cudaEvent_t)ev_begin, e = (cudaEvent_t)ev_end;
+  const bool had = g->ev_begin != nullptr;
+  g->ev_begin = b;
+  g->ev_end = e;
+  if (had && b && g->exec_one && g->node_ev_begin && !g->graphs_dirty) {
+    CK(cudaGraphExecEventRecordNodeSetEvent(g->exec_one, g->node_ev_begin, b));
+    CK(cudaGraphExecEventRecordNodeSetEvent(g->exec_one, g->node_ev_end, e));
+    return GBMD_OK;
+  }
+  destroy_graphs(g);   // rebuilt with (or without) the records at the next step
+  return GBMD_OK;
+}
+
+int gbmd_autotune(gbmd_system* s, const char* cache_path) {
+  if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
+  RET(use_device(s->device));
+  if (s->batch) return fail(GBMD_ERR_STATE, "system belongs to a batch");
+  RET(sync_system(s));
+  return autotune_group(s->own, cache_path);
+}
+
+int gbmd_set_tuning(gbmd_system* s, int32_t tpp, int32_t block) {
+  if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
+  RET(use_device(s->device));
+  RET(sync_system(s));
+  return set_tuning(s->own, tpp, block);
+}
+
+// ---- batches ----
+
+int gbmd_batch_create(int32_t precision, void* stream, int32_t device, gbmd_batch** out) {
+  if (!out || (precision != GBMD_FP64 && precision != GBMD_MIXED)) return fail(GBMD_ERR_BAD_ARG, "bad argument");
+  int dev = device;
+  if (dev < 0) CK(cudaGetDevice(&dev));
+  RET(use_device(dev));
+  Group* g = new Group();
+  g->device = dev;
+  g->is_batch = true;
+  g->precision = precision;
+  g->stream = (cudaStream_t)stream;
+  if (const char* ev = getenv("GBMD_NO_GRAPHS")) g->use_graphs = ev[0] != '1';
+  *out = reinterpret_cast<gbmd_batch*>(g);
+  return GBMD_OK;
+}
+
+int gbmd_batch_add(gbmd_batch* bh, gbmd_system* s, int32_t* slot) {
+  Group* b = reinterpret_cast<Group*>(bh);
+  if (!b || !s || !slot) return fail(GBMD_ERR_BAD_ARG, "NULL argument");
+  RET(use_device(reinterpret_cast<Group*>(bh)->device));
+  if (s->batch) return fail(GBMD_ERR_STATE, "system already in a batch");
+  if (s->h.precision != b->precision) return fail(GBMD_ERR_BAD_ARG, "precision mismatch");
+  if (s->device != b->device) return fail(GBMD_ERR_BAD_ARG, "system and batch are on different devices");
+  RET(sync_system(s));
+  CK(cudaStreamSynchronize(b->stream));
+  int k = -1;
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (!b->members[i]) { k = (int)i; break; }
+  if (k < 0) {
+    k = (int)b->members.size();
+    b->members.push_back(nullptr);
+  }
+  b->members[k] = s;
+  s->batch = b;
+  s->batch_slot = k;
+  s->own->stream = b->stream;
+  b->layout_dirty = true;
+  *slot = k;
+  return GBMD_OK;
+}
+
+int gbmd_batch_remove(gbmd_batch* bh, int32_t slot) {
+  Group* b = reinterpret_cast<Group*>(bh);
+  if (!b || slot < 0 || slot >= (int)b->members.size() || !b->members[slot])
+    return fail(GBMD_ERR_BAD_ARG, "bad slot");
+  RET(use_device(reinterpret_cast<Group*>(bh)->device));
+  gbmd_system* s = b->members[slot];
+  RET(sync_system(s));
+  CK(cudaStreamSynchronize(b->stream));
+  b->members[slot] = nullptr;
+  s->batch = nullptr;
+  s->batch_slot = -1;
+  s->own->stream = s->stream;
+  b->layout_dirty = true;
+  return GBMD_OK;
+}
+
+int gbmd_batch_step(gbmd_batch* bh, int64_t nsteps) {
+  Group* b = reinterpret_cast<Group*>(bh);
+  if (!b || nsteps < 0) return fail(GBMD_ERR_BAD_ARG, "bad argument");
+  RET(use_device(reinterpret_cast<Group*>(bh)->device));
+  for (auto* s : live(b)) s->target_step += nsteps;
+  return enqueue_steps(b, nsteps);
+}
+
+int gbmd_batch_sync(gbmd_batch* bh) {
+  Group* b = reinterpret_cast<Group*>(bh);
+  if (!b) return fail(GBMD_ERR_BAD_ARG, "NULL batch");
+  RET(use_device(reinterpret_cast<Group*>(bh)->device));
+  CK(cudaStreamSynchronize(b->stream));
+  int first = GBMD_OK;
+  std::string msg;
+  for (auto* s : live(b)) {
+    int rc = sync_system(s);
+    if (rc != GBMD_OK && first == GBMD_OK) {
+      first = rc;
+      msg = g_err;
+    }
+  }
+  if (first != GBMD_OK) g_err = msg;
+  return first;
+}
+
+int gbmd_batch_autotune(gbmd_batch* bh, const char* cache_path) {
+  Group* b = reinterpret_cast<Group*>(bh);
+  if (!b) return fail(GBMD_ERR_BAD_ARG, "NULL batch");
+  RET(use_device(reinterpret_cast<Group*>(bh)->device));
+  RET(gbmd_batch_sync(bh));
+  if (live(b).empty()) return GBMD_OK;
+  return autotune_group(b, cache_path);
+}
+
+int gbmd_batch_set_tuning(gbmd_batch* bh, int32_t tpp, int32_t block) {
+  Group* b = reinterpret_cast<Group*>(bh);
+  if (!b) return fail(GBMD_ERR_BAD_ARG, "NULL batch");
+  RET(use_device(reinterpret_cast<Group*>(bh)->device));
+  RET(gbmd_batch_sync(bh));
+  return set_tuning(b, tpp, block);
+}
+
+int gbmd_batch_info(gbmd_batch* bh, int32_t* members, int64_t* particles, int64_t* launches) {
+  Group* b = reinterpret_cast<Group*>(bh);
+  if (!b) return fail(GBMD_ERR_BAD_ARG, "NULL batch");
+  RET(use_device(reinterpret_cast<Group*>(bh)->device));
+  std::vector<gbmd_system*> m = live(b);
+  if (members) *members = (int32_t)m.size();
+  if (particles) {
+    int64_t np = 0;
+    for (auto* s : m) np += s->h.n;
+    *particles = np;
+  }
+  if (launches) {
+    GroupCtl c{};
+    if (b->d_ctl) {
+      CK(cudaMemcpyAsync(&c, b->d_ctl, sizeof(c), cudaMemcpyDeviceToHost, b->stream));
+      CK(cudaStreamSynchronize(b->stream));
+    }
+    *launches = (int64_t)c.launches;
+  }
+  return GBMD_OK;
+}
+
+int gbmd_batch_destroy(gbmd_batch* bh) {
+  Group* b = reinterpret_cast<Group*>(bh);
+  if (!b) return fail(GBMD_ERR_BAD_ARG, "NULL batch");
+  use_device(b->device);
+  cudaStreamSynchronize(b->stream);
+  for (auto* s : live(b)) {
+    s->batch = nullptr;
+    s->batch_slot = -1;
+    s->own->stream = s->stream;
+  }
+  destroy_graphs(b);
+  cudaFree(b->d_desc); cudaFree(b->d_tp); cudaFree(b->d_tf); cudaFree(b->d_tc);
+  cudaFree(b->d_ts); cudaFree(b->d_partials); cudaFree(b->d_ctl);
+  delete b;
+  return GBMD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// gbmd_internal.cuh -- device-side data layout shared by the kernels of libgbmd.
+//
+// Every kernel walks a tile table (system, first, count) over a device array of
+// SysDev descriptors, so one launch serves one system or a whole batch, and the
+// descriptors (not the launch arguments) hold buffer pointers and sizes: a
+// captured CUDA graph stays valid when a buffer is re-allocated (neighbour-list
+// growth) because only the descriptor in device memory changes.
+//
+// Data layout per system (N particles, current internal order):
+//   x, v        FP64 planar [3][N] (x wrapped into [-L/2, L/2); v lags half a kick
+//               behind the full-step velocity unless flags->v_full)
+//   img         int32 planar [3][N] periodic image counts
+//   type, tag   int32 [N]; rtag int32 [N] (tag -> internal index)
+//   q           int4 [N]: x as 32-bit fixed point of x/L (2^32 <-> L, two's
+//               complement, so an int32 difference is the minimum image) + type in w
+//   q_build     int4 [N]: q at the last neighbour-list build (displacement check)
+//   p64         double4_32a [N]: FP64 x, y, z + type bits in w (FP64 force gather only)
+//   f32 / f64   float4 / double4_32a [N]: force (+ per-particle energy in w when asked)
+//   nn, nl      int32 [N] neighbour counts; int32 [N][cap] rows (row-major)
+//   cell arrays key [N] (cell rank), cnt/start/cursor [ncells+1], members [N]
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gbmd.h"
+
+namespace gbmd {
+
+constexpr int MAXT = GBMD_MAX_TYPES;
+constexpr int MAXT2 = MAXT * MAXT;
+
+// error codes stored in Flags::error (positive on the device)
+enum DevError : int { DEV_OK = 0, DEV_OVERFLOW = 1, DEV_NONFINITE = 2, DEV_BADTYPE = 3 };
+
+struct Flags {
+  int rebuild_req;          // set by the integrate kernel when r_buff/2 is exceeded
+  int do_rebuild;           // this step rebuilds (decided once per step)
+  int do_sort;              // this step re-sorts (Morton cell order) before building
+  int active;               // this step advances the system
+  int error;                // DevError; nonzero freezes the system
+  int overflow_need;        // largest neighbour count seen in an overflowing build
+  int v_full;               // 1: v holds full-step velocities (after create / set_state)
+  int pad0;
+  long long step;           // steps completed
+  long long step_limit;     // -1 = none
+  long long last_sort;      // step of the last Morton re-sort
+  long long n_rebuilds;
+  long long n_sorts;
+  unsigned long long launches;   // kernels executed for this system
+  unsigned long long nb_total;   // sum of neighbour counts at the last build
+};
+
+// pair coefficients: lj1 = 48 eps sigma^12, lj2 = 24 eps sigma^6 (force/r factors),
+// c12 = 4 eps sigma^12, c6 = 4 eps sigma^6, shift = V_LJ(r_cut)
+struct PairF { float lj1, lj2, rc2, pad; float c12, c6, shift, rl2; };
+struct PairD { double lj1, lj2, rc2, rl2; double c12, c6, shift, pad; };
+
+struct SysDev {
+  // geometry
+  double L[3], halfL[3];
+  double qscale[3];        // 2^32 / L
+  float fscale[3];         // L / 2^32
+  float rbuff_half2;       // (r_buff / 2)^2, slightly reduced (conservative)
+  int nc[3];               // cells per axis
+  int ncells;
+  int n, ntypes, cap, precision;
+  int sort_period;
+  double dt, h;            // h = dt / (2 m)
+  double mass;
+  // per type pair
+  PairF pf[MAXT2];
+  PairD pd[MAXT2];
+  // particle arrays
+  double *x, *v;
+  int *img, *type, *tag, *rtag;
+  int4 *q, *q_build;
+  double4_32a *p64;
+  float4 *f32;
+  double4_32a *f64;
+  int *nn, *nl;
+  // cell list
+  int *key, *cell_cnt, *cell_start, *cell_cursor, *members, *members_tmp;
+  const int *rank2lin, *lin2rank;
+  // re-sort scratch (same layout as the primaries)
+  double *x_alt, *v_alt;
+  int *img_alt, *type_alt, *tag_alt;
+  int4 *q_alt;
+  // thermo scratch: per-force-tile partial sums (pe, virial[6], pad) and output
+  double *partials;
+  int tile_first_f, tile_count_f;   // this system's tiles in the force tile table
+  double *thermo;                   // 16 doubles: pe, ke, virial[6], ...
+  double *pp_u, *pp_w;              // optional per-particle energy / virial (N, N x 6)
+  Flags *flags;
+};
+
+// group-level control block (one per single system or batch)
+struct GroupCtl {
+  unsigned int blocks_done;  // last-block counter of the integrate kernel
+  int any_rebuild;
+  unsigned long long launches;
+};
+
+struct Tile { int sys, first, count, pad; };
+
+// ---- device helpers -------------------------------------------------------
+
+__device__ __forceinline__ void count_launch(const SysDev& s) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&s.flags->launches, 1ull);
+}
+
+// 32-bit fixed point of x/L with wrap-around; x in any image
+__device__ __forceinline__ int to_fixed(double x, double qscale) {
+  long long q = __double2ll_rn(x * qscale);
+  return (int)(unsigned int)(unsigned long long)q;
+}
+
+__device__ __forceinline__ int min_image_fixed(int a, int b) {
+  return (int)((unsigned int)a - (unsigned int)b);
+}
+
+// cell coordinate of a fixed-point coordinate: floor((q + 2^31) * nc / 2^32)
+__device__ __forceinline__ int cell_of_fixed(int q, int nc) {
+  unsigned long long u = (unsigned long long)((unsigned int)q ^ 0x80000000u);
+  return (int)((u * (unsigned long long)nc) >> 32);
+}
+
+}  // namespace gbmd

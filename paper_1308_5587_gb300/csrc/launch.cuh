@@ -1,0 +1,62 @@
+// launch.cuh -- host-side launchers of the libgbmd kernels (one per kernel family).
+// Every launcher enqueues on `st` and returns the launch status; none allocates.
+// Grids are tile counts: each block handles one Tile of its table.
+#pragma once
+#include "gbmd_internal.cuh"
+
+namespace gbmd {
+
+constexpr int TILE_P = 256;     // particles per block of the streaming kernels
+constexpr int CELLS_PER_TILE = 8;   // warps (= cells) per block of the cell kernels
+constexpr int SCAN_THREADS = 1024;
+
+// kernel-node description for graph building: function + grid + argument values.
+// Copyable: the pointer array that cudaLaunchKernel / kernel nodes want is built
+// from `store` at the point of use (args_of), never kept inside the object.
+struct KernelCall {
+  void* func;
+  dim3 grid, block;
+  size_t smem;
+  int nargs;
+  alignas(16) unsigned char store[10][16];
+};
+
+inline void args_of(const KernelCall& k, void** a) {
+  for (int i = 0; i < k.nargs; ++i) a[i] = const_cast<unsigned char*>(k.store[i]);
+}
+
+// integrate (K6): kick(s) + drift + wrap + fixed-point shadow + displacement check;
+// the last block decides per-system activity/rebuild/sort for the step and, when
+// use_cond, sets the graph conditional that gates the rebuild.
+KernelCall integrate_call(int prec, const SysDev* d, const Tile* tiles, int ntiles, GroupCtl* ctl,
+                          int nsys, cudaGraphConditionalHandle cond, int use_cond);
+// cell list + sort + neighbour list (each a no-op for systems not rebuilding)
+KernelCall bin_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
+KernelCall scan_call(const SysDev* d, const Tile* tiles_s, int nsys, GroupCtl* ctl);
+KernelCall scatter_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
+KernelCall cellsort_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl* ctl);
+KernelCall permute_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
+KernelCall copyback_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
+KernelCall nlist_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl* ctl);
+// pair force (K5): ev = 0 forces only, 1 also energy/virial partial sums
+// (+ per-particle arrays when the descriptor has them); force_all ignores the
+// per-step activity flag (used outside the step graph)
+KernelCall force_call(int prec, int multi, int ev, int tpp, int block, const SysDev* d,
+                      const Tile* tiles_f, int ntiles, GroupCtl* ctl, int force_all);
+// thermo reduction (K7), one block per system
+KernelCall thermo_call(const SysDev* d, const Tile* tiles_s, int nsys, GroupCtl* ctl);
+// import row-major tag-order staging -> internal arrays; export the reverse
+KernelCall import_call(const SysDev* d, const Tile* tiles_p, int ntiles, const double* pos,
+                       const double* vel, const int* type, const int* image);
+KernelCall export_call(const SysDev* d, const Tile* tiles_p, int ntiles, double* pos,
+                       double* vel, int* image, double* force, double* pp_u, double* pp_w);
+// neighbour rows -> tag-order rows sorted ascending (test readout)
+KernelCall nlist_export_call(const SysDev* d, const Tile* tiles_p, int ntiles, int* counts,
+                             int* idx, int cap_out, int* too_many);
+
+cudaError_t launch(const KernelCall& k, cudaStream_t st);
+
+// force-kernel variants available (threads per particle)
+bool tpp_supported(int tpp);
+
+}  // namespace gbmd

@@ -1,0 +1,92 @@
+"""The C-ABI library builds, loads and exports every symbol include/gbmd.h declares;
+host-side argument checks run without a GPU (no compute is launched here)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbmd.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1308_5587_gb300 import _build, gbmd
+    _build.build()
+    return gbmd
+
+
+def declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(gbmd_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for must in ("gbmd_create", "gbmd_step", "gbmd_get_forces", "gbmd_get_thermo",
+                 "gbmd_get_state", "gbmd_set_state", "gbmd_get_neighbors",
+                 "gbmd_footprint_bytes", "gbmd_batch_create", "gbmd_batch_add",
+                 "gbmd_batch_remove", "gbmd_batch_step", "gbmd_autotune", "gbmd_destroy",
+                 "gbmd_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import ctypes
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in declared() if not hasattr(so, n)]
+    assert not missing, missing
+    assert set(declared()) <= set(lib._SIGS)
+
+
+def test_abi_version(lib):
+    assert lib.gbmd_abi_version() == 1
+
+
+def _desc(lib, **over):
+    n = over.pop("n", 4)
+    pos = over.pop("pos", np.zeros((n, 3)))
+    vel = np.zeros((n, 3))
+    kw = dict(box=over.pop("box", 20.0), types=over.pop("types", None), eps=over.pop("eps", 1.0),
+              sigma=1.0, rcut=over.pop("rcut", 2.5), r_buff=0.4, dt=over.pop("dt", 0.005),
+              mass=1.0, precision=over.pop("precision", "mixed"))
+    return lib.make_desc(n, kw["box"], pos, vel, kw["types"], kw["eps"], kw["sigma"], kw["rcut"],
+                         kw["r_buff"], kw["dt"], kw["mass"], kw["precision"], **over)
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(dt=0.0), "BAD_ARG"),
+    (dict(dt=-1.0), "BAD_ARG"),
+    (dict(box=5.0), "BOX_TOO_SMALL"),
+    (dict(rcut=-1.0), "BAD_ARG"),
+    (dict(precision=7), "BAD_ARG"),
+    (dict(types=np.array([0, 1, 0, 0], np.int32)), "BAD_ARG"),      # type >= ntypes
+    (dict(pos=np.full((4, 3), np.nan)), "BAD_ARG"),
+    (dict(threads_per_particle=3), "BAD_ARG"),
+    (dict(eps=np.array([[1.0, 2.0], [1.5, 1.0]])), "BAD_ARG"),     # not symmetric
+])
+def test_create_rejects_bad_arguments_on_the_host(lib, bad, status):
+    d, keep = _desc(lib, **bad)
+    with pytest.raises(lib.GbmdError) as e:
+        lib.gbmd_create(d)
+    assert e.value.status == status
+    assert lib.gbmd_last_error()
+
+
+def test_null_arguments(lib):
+    L = lib.load()
+    import ctypes
+    assert L.gbmd_create(None, ctypes.byref(ctypes.c_void_p())) == -1
+    assert L.gbmd_step(None, 1) == -1
+    assert L.gbmd_destroy(None) == -1
+    assert "NULL" in lib.gbmd_last_error()
+
+
+def test_footprint_is_host_side_and_monotone(lib):
+    a, k1 = _desc(lib, n=1000, box=12.0)
+    b, k2 = _desc(lib, n=8000, box=24.0)
+    fa, fb = lib.gbmd_footprint_bytes(a), lib.gbmd_footprint_bytes(b)
+    assert 0 < fa < fb
+    # about 0.7-1.2 KB per particle for the default capacity at liquid density
+    assert 300 < fb / 8000 < 3000
