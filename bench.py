@@ -344,7 +344,9 @@ def gpu_arm(args):
                       "parallelism": f"replicas x{world}" if world > 1 else "single system",
                       "l2": "flushed between steps (256 MB write)" if flush is not None
                       else "inputs larger than L2 (nlist > 129 MB)",
-                      "timed_iteration": "one MD step (one single-step CUDA graph)",
+                      "timed_iteration": "one MD step (" + ("direct kernel launches" if
+                                                            args.no_graphs else
+                                                            "one single-step CUDA graph") + ")",
                       "threads_per_particle": info["threads_per_particle"],
                       "force_block": info["force_block"], "nlist_capacity": info["nlist_capacity"],
                       "sort_period": sort_period},
@@ -452,7 +454,12 @@ def main(argv=None):
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the same kernels directly instead of through CUDA graphs "
+                         "(ncu cannot profile kernels inside graphs with conditional nodes)")
     args = ap.parse_args(argv)
+    if args.no_graphs:
+        os.environ["GBMD_NO_GRAPHS"] = "1"
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
