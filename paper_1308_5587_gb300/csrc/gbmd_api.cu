@@ -304,7 +304,10 @@ int enqueue_steps(Group* g, long long n) {
   for (long long k = 0; k < n; ++k) {
     CK(launch(integrate_call(g->precision, g->d_desc, g->d_tp, g->ntp, g->d_ctl, nsys, 0, 0), g->stream));
     for (const KernelCall& c : rebuild_calls(g)) CK(launch(c, g->stream));
+    const bool events = n == 1 && g->ev_begin && g->ev_end;
+    if (events) CK(cudaEventRecord(g->ev_begin, g->stream));
     CK(launch(step_force_call(g, 0, 0), g->stream));
+    if (events) CK(cudaEventRecord(g->ev_end, g->stream));
   }
   return GBMD_OK;
 }
