@@ -157,6 +157,33 @@ int gbmd_get_forces(gbmd_system *s, double *out);
 /* Energy, virial, temperature and pressure at the current step. */
 int gbmd_get_thermo(gbmd_system *s, gbmd_thermo *out);
 
+/* Allocation-free variant of gbmd_get_thermo, for callers that must not allocate
+ * GPU memory: applications whose memory manager has reserved the device's memory
+ * up front (so a driver allocation would fail or fragment its pool) and code
+ * that runs while another thread captures CUDA work in a mode where cudaMalloc
+ * is an error.  The paper has no counterpart; it is part of this library's API
+ * only.  It runs the same energy/virial kernels as gbmd_get_thermo, but their
+ * per-tile partial sums and the system descriptor they read live in static
+ * device arrays of this library (2 MiB + one descriptor, held on every device
+ * that loads the library until the process exits) instead of in buffers the
+ * library allocates.  Limits and behaviour:
+ *   - systems with more than GBMD_NOALLOC_MAX_TILES force-kernel tiles (one tile
+ *     = force block / threads per particle particles, 32 at the default tuning,
+ *     so about one million particles) are rejected with GBMD_ERR_BAD_ARG;
+ *   - the first call on a device looks up the static arrays' device addresses
+ *     (cudaGetSymbolAddress), once; make that first call before any stream
+ *     capture begins;
+ *   - it never grows buffers: if the system has a pending neighbour-list
+ *     overflow or changed layout it returns GBMD_ERR_STATE (call gbmd_sync or
+ *     gbmd_get_thermo once first); non-finite state gives GBMD_ERR_NONFINITE;
+ *   - every call shares the static arrays, which keep the last call's contents
+ *     (each call overwrites everything it reads, so nothing needs clearing);
+ *     calls whose GPU work overlaps -- from two threads, or on two streams --
+ *     race on them and must be serialised by the caller.
+ * Output as gbmd_get_thermo (same kernels, same summation order). */
+#define GBMD_NOALLOC_MAX_TILES 32768
+int gbmd_get_thermo_noalloc(gbmd_system *s, gbmd_thermo *out);
+
 /* Per-particle energy (n, half of every pair energy) and virial (n x 6, half of
  * every pair virial), tag order; either pointer may be NULL. */
 int gbmd_get_per_particle(gbmd_system *s, double *energy, double *virial);

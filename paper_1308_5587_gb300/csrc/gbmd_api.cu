@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -1174,3 +1175,93 @@ int gbmd_batch_destroy(gbmd_batch* bh) {
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Allocation-free thermo readout (gbmd_get_thermo_noalloc)
+//
+// For callers that may not allocate GPU memory.  The scratch the energy/virial
+// kernels need -- per-tile FP64 partial sums and the descriptor copy they read --
+// lives in the static device arrays below; host code only ever passes their
+// device addresses (looked up once per device with cudaGetSymbolAddress), never
+// the symbols themselves.
+// ============================================================================
+namespace {
+
+constexpr int kNoallocMaxTiles = GBMD_NOALLOC_MAX_TILES;
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_partials[8 * kNoallocMaxTiles];   // 2 MiB
+static __device__ __align__(256) SysDev g_noalloc_desc;
+
+struct NoallocAddrs {
+  bool ready = false;
+  double* partials = nullptr;
+  SysDev* desc = nullptr;
+};
+NoallocAddrs g_noalloc_addrs[kNoallocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+// once per device, with that device current
+int noalloc_setup(int dev, NoallocAddrs* out) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(GBMD_ERR_BAD_ARG, "device ordinal %d too large", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  NoallocAddrs& a = g_noalloc_addrs[dev];
+  if (!a.ready) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return fail(GBMD_ERR_CUDA, "cudaGetSymbolAddress(partials): %s", cudaGetErrorString(e));
+    a.partials = static_cast<double*>(p);
+    e = cudaGetSymbolAddress(&p, g_noalloc_desc);
+    if (e != cudaSuccess) return fail(GBMD_ERR_CUDA, "cudaGetSymbolAddress(descriptor): %s", cudaGetErrorString(e));
+    a.desc = static_cast<SysDev*>(p);
+    a.ready = true;
+  }
+  *out = a;
+  return GBMD_OK;
+}
+
+}  // namespace
+
+extern "C" int gbmd_get_thermo_noalloc(gbmd_system* s, gbmd_thermo* out) {
+  if (!s || !out) return fail(GBMD_ERR_BAD_ARG, "NULL argument");
+  RET(use_device(s->device));
+  NoallocAddrs addr;
+  RET(noalloc_setup(s->device, &addr));
+  Group* g = s->own;
+  cudaStream_t st = g->stream;
+  // finish queued work without any recovery that could allocate
+  CK(cudaStreamSynchronize(st));
+  Flags f;
+  RET(read_flags(s, &f, st));
+  if (f.error == DEV_NONFINITE) return fail(GBMD_ERR_NONFINITE, "non-finite state (step %lld)", f.step);
+  if (f.error) return fail(GBMD_ERR_STATE, "pending device error %d: call gbmd_sync first", f.error);
+  long long want = s->target_step;
+  if (s->step_limit >= 0) want = std::min(want, s->step_limit);
+  if (f.step < want) return fail(GBMD_ERR_STATE, "steps still owed after a recovery: call gbmd_sync first");
+  if (g->layout_dirty) return fail(GBMD_ERR_STATE, "layout changed: call gbmd_sync or gbmd_get_thermo first");
+  if (g->ntf > kNoallocMaxTiles)
+    return fail(GBMD_ERR_BAD_ARG, "%d force tiles exceed the allocation-free limit of %d", g->ntf, kNoallocMaxTiles);
+  // the system's descriptor, pointed at the static partials (own group: tiles from 0)
+  SysDev d = s->h;
+  d.tile_first_f = 0;
+  d.tile_count_f = g->ntf;
+  d.partials = addr.partials;
+  CK(cudaMemcpyAsync(addr.desc, &d, sizeof(SysDev), cudaMemcpyHostToDevice, st));
+  CK(launch(force_call(g->precision, g->multi, 1, g->tpp, g->fblock, addr.desc, g->d_tf, g->ntf,
+                       g->d_ctl, 1), st));
+  CK(launch(thermo_call(addr.desc, g->d_ts, g->nts, g->d_ctl), st));
+  double t[8];
+  CK(cudaMemcpyAsync(t, s->d_thermo, sizeof(t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));   // `d` and `t` are host stack memory
+  const double n = (double)s->h.n;
+  const double vol = s->h.L[0] * s->h.L[1] * s->h.L[2];
+  out->step = f.step;
+  out->pe = t[0];
+  out->ke = 0.5 * s->h.mass * t[1];
+  out->temperature = n > 1 ? 2.0 * out->ke / (3.0 * n - 3.0) : 0.0;
+  for (int c = 0; c < 6; ++c) out->virial[c] = t[2 + c];
+  out->w = t[2] + t[5] + t[7];
+  out->pressure = (n * out->temperature + out->w / 3.0) / vol;
+  out->n_rebuilds = f.n_rebuilds;
+  return GBMD_OK;
+}

@@ -77,6 +77,7 @@ _SIGS = {
     "gbmd_sync": (C.c_int, [C.c_void_p]),
     "gbmd_get_forces": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gbmd_get_thermo": (C.c_int, [C.c_void_p, C.POINTER(gbmd_thermo)]),
+    "gbmd_get_thermo_noalloc": (C.c_int, [C.c_void_p, C.POINTER(gbmd_thermo)]),
     "gbmd_get_per_particle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gbmd_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.POINTER(C.c_int64)]),
@@ -217,6 +218,13 @@ def gbmd_get_forces(h, n: int, out=None):
 def gbmd_get_thermo(h) -> dict:
     t = gbmd_thermo()
     _check(load().gbmd_get_thermo(h, C.byref(t)))
+    return t.as_dict()
+
+
+def gbmd_get_thermo_noalloc(h) -> dict:
+    """gbmd_get_thermo without any GPU allocation (static scratch; see gbmd.h)."""
+    t = gbmd_thermo()
+    _check(load().gbmd_get_thermo_noalloc(h, C.byref(t)))
     return t.as_dict()
 
 
