@@ -87,7 +87,8 @@ typedef struct gbmd_desc {
                                    rebuild at least this many steps after the last sort;
                                    0 = sort only when the system is created */
     int32_t nlist_capacity;     /* neighbours per particle to reserve; 0 = from density */
-    int32_t threads_per_particle; /* 0 = default (8); else 4, 8, 16 or 32 */
+    int32_t threads_per_particle; /* lanes per particle in the force kernel:
+                                     0 = default (2); else 1, 2 or 4 */
     void *stream;               /* cudaStream_t to run on; NULL = the legacy default stream */
     int32_t device;             /* CUDA device ordinal; -1 = the calling thread's current
                                    device.  Every later call on the system uses it. */
@@ -168,8 +169,8 @@ int gbmd_get_thermo(gbmd_system *s, gbmd_thermo *out);
  * that loads the library until the process exits) instead of in buffers the
  * library allocates.  Limits and behaviour:
  *   - systems with more than GBMD_NOALLOC_MAX_TILES force-kernel tiles (one tile
- *     = force block / threads per particle particles, 32 at the default tuning,
- *     so about one million particles) are rejected with GBMD_ERR_BAD_ARG;
+ *     = force block / threads per particle particles, 128 at the default tuning,
+ *     so about four million particles) are rejected with GBMD_ERR_BAD_ARG;
  *   - the first call on a device looks up the static arrays' device addresses
  *     (cudaGetSymbolAddress), once; make that first call before any stream
  *     capture begins;
@@ -219,8 +220,8 @@ int gbmd_set_step_limit(gbmd_system *s, int64_t step);
  * count, size and density class. */
 int gbmd_autotune(gbmd_system *s, const char *cache_path);
 
-/* Set the force kernel's threads per particle (1,2,4,8,16,32) and block size
- * (64..1024, a multiple of 32 and of tpp) explicitly. */
+/* Set the force kernel's threads per particle (1, 2 or 4) and block size
+ * (32..512, a multiple of 32) explicitly. */
 int gbmd_set_tuning(gbmd_system *s, int32_t threads_per_particle, int32_t block);
 
 /* Bracket the force kernel of every subsequent single step (gbmd_step(s, 1)) with

@@ -84,8 +84,9 @@ struct Group {
   bool is_batch = false;
   int precision = GBMD_MIXED;
   int multi = 0;
+  bool rel = true;     // every member has at least 3 cells on every axis
   cudaStream_t stream = nullptr;
-  int tpp = 8, fblock = 256;
+  int tpp = 2, fblock = 256;
   // device tables
   SysDev* d_desc = nullptr;
   Tile *d_tp = nullptr, *d_tf = nullptr, *d_tc = nullptr, *d_ts = nullptr;
@@ -149,6 +150,7 @@ int sync_layout(Group* g) {
   std::vector<Tile> tp, tf, tc, ts;
   const int per_f = g->fblock / g->tpp;
   g->multi = 0;
+  g->rel = true;
   for (size_t k = 0; k < m.size(); ++k) {
     SysDev d = m[k]->h;
     const int n = d.n;
@@ -161,6 +163,7 @@ int sync_layout(Group* g) {
     ts.push_back({(int)k, 0, 0, 0});
     desc.push_back(d);
     if (d.ntypes > 1) g->multi = 1;
+    if (d.nc[0] < 3 || d.nc[1] < 3 || d.nc[2] < 3) g->rel = false;
   }
   RET(grow(&g->d_partials, &g->cap_part, 8 * std::max<size_t>(tf.size(), 1)));
   for (auto& d : desc) d.partials = g->d_partials;
@@ -205,7 +208,7 @@ std::vector<KernelCall> rebuild_calls(const Group* g) {
           cellsort_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl),
           permute_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
           copyback_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
-          nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl)};
+          nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi)};
 }
 
 KernelCall step_force_call(const Group* g, int ev, int force_all) {
@@ -352,11 +355,11 @@ int grow_nlist(gbmd_system* s, int need) {
   auto it = std::find(s->allocs.begin(), s->allocs.end(), (void*)s->h.nl);
   if (it != s->allocs.end()) {
     s->allocs.erase(it);
-    s->footprint -= (size_t)s->h.n * s->h.cap * sizeof(int);
+    s->footprint -= (size_t)s->h.nl_stride * s->h.cap * sizeof(int);
   }
   CK(cudaFree(s->h.nl));
   s->h.nl = nullptr;
-  RET(dalloc(s, (void**)&s->h.nl, (size_t)s->h.n * cap * sizeof(int)));
+  RET(dalloc(s, (void**)&s->h.nl, (size_t)s->h.nl_stride * cap * sizeof(int)));
   s->h.cap = cap;
   return refresh_desc(s);
 }
@@ -404,7 +407,7 @@ int validate(const gbmd_desc* d, bool device) {
   if (d->precision != GBMD_FP64 && d->precision != GBMD_MIXED) return fail(GBMD_ERR_BAD_ARG, "precision must be GBMD_FP64 or GBMD_MIXED");
   if (d->sort_period < 0 || d->nlist_capacity < 0) return fail(GBMD_ERR_BAD_ARG, "sort_period and nlist_capacity must be >= 0");
   if (d->threads_per_particle != 0 && !tpp_supported(d->threads_per_particle))
-    return fail(GBMD_ERR_BAD_ARG, "threads_per_particle must be 0, 4, 8, 16 or 32");
+    return fail(GBMD_ERR_BAD_ARG, "threads_per_particle must be 0, 1, 2 or 4");
   const int nt = d->ntypes;
   double rmax = 0;
   for (int a = 0; a < nt; ++a)
@@ -451,7 +454,7 @@ Geometry geometry(const gbmd_desc* d) {
     g.ncells *= g.nc[a];
   }
   if (d->nlist_capacity > 0) {
-    g.cap = d->nlist_capacity;
+    g.cap = (int)round_up((size_t)d->nlist_capacity, 4);   // whole slot groups
   } else {
     const double rho = (double)d->n / (d->box[0] * d->box[1] * d->box[2]);
     const double nexp = rho * 4.0 / 3.0 * M_PI * g.rl_max * g.rl_max * g.rl_max;
@@ -478,7 +481,7 @@ size_t footprint_of(const gbmd_desc* d, const Geometry& g) {
   b += n * 16 * 2;               // q, q_build
   b += n * 32;                   // p64
   b += n * (d->precision == GBMD_FP64 ? 32 : 16);   // force
-  b += n * 4 + n * 4 * (size_t)g.cap;                // nn, nl
+  b += n * 4 + round_up(n, 32) * 4 * (size_t)g.cap;  // nn, nl (ELL4)
   b += n * 4 * 3 + (size_t)(g.ncells + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;  // cells
   b += n * (8 * 3 * 2 + 4 * 3 + 4 * 2 + 16);         // re-sort scratch
   b += n * (8 * 3 * 3 + 4 * 3 + 4 * 2);              // import/export staging
@@ -507,6 +510,7 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   h.precision = d->precision;
   h.sort_period = d->sort_period;
   h.cap = geo.cap;
+  h.nl_stride = (int)round_up((size_t)n, 32);
   h.dt = d->dt;
   h.mass = d->mass;
   h.h = 0.5 * d->dt / d->mass;
@@ -553,7 +557,7 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   A((void**)&h.type, N * 4); A((void**)&h.tag, N * 4); A((void**)&h.rtag, N * 4);
   A((void**)&h.q, N * 16); A((void**)&h.q_build, N * 16); A((void**)&h.p64, N * 32);
   if (d->precision == GBMD_FP64) A((void**)&h.f64, N * 32); else A((void**)&h.f32, N * 16);
-  A((void**)&h.nn, N * 4); A((void**)&h.nl, N * 4 * (size_t)geo.cap);
+  A((void**)&h.nn, N * 4); A((void**)&h.nl, round_up(N, 32) * 4 * (size_t)geo.cap);
   A((void**)&h.key, N * 4); A((void**)&h.members, N * 4); A((void**)&h.members_tmp, N * 4);
   A((void**)&h.cell_cnt, (geo.ncells + 1) * 4); A((void**)&h.cell_start, (geo.ncells + 1) * 4);
   A((void**)&h.cell_cursor, (geo.ncells + 1) * 4);
@@ -738,7 +742,7 @@ std::string tune_key(const Group* g) {
 }
 
 int set_tuning(Group* g, int tpp, int block) {
-  if (!tpp_supported(tpp) || block < 64 || block > 1024 || block % 32 || block % tpp)
+  if (!tpp_supported(tpp) || block < 32 || block > 512 || block % 32 || block % tpp)
     return fail(GBMD_ERR_BAD_ARG, "bad tuning tpp=%d block=%d", tpp, block);
   if (g->tpp == tpp && g->fblock == block) return GBMD_OK;
   g->tpp = tpp;
@@ -764,11 +768,12 @@ int autotune_group(Group* g, const char* cache) {
   }
   int best_t = g->tpp, best_b = g->fblock;
   float best = 1e30f;
-  for (int tpp : {4, 8, 16, 32})
+  for (int tpp : {1, 2, 4})
     for (int block : {128, 256, 512}) {
       RET(set_tuning(g, tpp, block));
       float ms;
       RET(time_force(g, &ms));
+      if (getenv("GBMD_VERBOSE")) fprintf(stderr, "gbmd autotune %s tpp=%d block=%d %.4f ms\n", key.c_str(), tpp, block, ms);
       if (ms < best) { best = ms; best_t = tpp; best_b = block; }
     }
   RET(set_tuning(g, best_t, best_b));

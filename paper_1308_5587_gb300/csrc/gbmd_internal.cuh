@@ -16,7 +16,9 @@
 //   q_build     int4 [N]: q at the last neighbour-list build (displacement check)
 //   p64         double4_32a [N]: FP64 x, y, z + type bits in w (FP64 force gather only)
 //   f32 / f64   float4 / double4_32a [N]: force (+ per-particle energy in w when asked)
-//   nn, nl      int32 [N] neighbour counts; int32 [N][cap] rows (row-major)
+//   nn, nl      int32 [N] neighbour counts; ELL4 list: entry k of particle i at
+//               nl[((k / 4) * nl_stride + i) * 4 + k % 4], nl_stride = N rounded up
+//               to 32, cap (a multiple of 4) entries per particle
 //   cell arrays key [N] (cell rank), cnt/start/cursor [ncells+1], members [N]
 #pragma once
 #include <cstdint>
@@ -64,6 +66,7 @@ struct SysDev {
   int nc[3];               // cells per axis
   int ncells;
   int n, ntypes, cap, precision;
+  int nl_stride;           // particles per slot group of the ELL4 list (N rounded up to 32)
   int sort_period;
   double dt, h;            // h = dt / (2 m)
   double mass;
@@ -116,6 +119,11 @@ __device__ __forceinline__ int to_fixed(double x, double qscale) {
 
 __device__ __forceinline__ int min_image_fixed(int a, int b) {
   return (int)((unsigned int)a - (unsigned int)b);
+}
+
+// address of entry k of particle i in the ELL4 neighbour list
+__device__ __forceinline__ size_t nl_index(int i, int k, int stride) {
+  return ((size_t)(k >> 2) * (size_t)stride + (size_t)i) * 4 + (size_t)(k & 3);
 }
 
 // cell coordinate of a fixed-point coordinate: floor((q + 2^31) * nc / 2^32)

@@ -15,7 +15,8 @@
 //     j != i with r^2 < r_list,ij^2 (strict), r_list,ij = r_cut,ij + r_buff.  The
 //     test runs in FP32 on the fixed-point difference; candidates within a relative
 //     band of 1e-5 of r_list^2 are decided again in FP64 with the same operations
-//     (and rounding) as the brute-force reference definition.
+//     (and rounding) as the brute-force reference definition, and appended after
+//     the other hits of their chunk of 32 candidates.
 #include "launch.cuh"
 
 namespace gbmd {
@@ -210,70 +211,189 @@ __device__ __noinline__ bool exact_within(const SysDev& s, int i, int j, double 
 }
 
 // ---- neighbour list: one warp per cell ----
+// Lanes are the cell's particles (up to 32 at a time).  The candidates -- the
+// members of the stencil cells in (dz, dy, dx) cell order and index order within
+// a cell, flattened into one stream -- pass through a per-warp shared-memory
+// buffer 32 at a time, each converted once into FP32 coordinates relative to the
+// centre of the warp's cell (the fixed-point difference takes care of the
+// periodic wrap) plus j | type << 30; the next chunk is loaded while the current
+// one is tested.  Every lane then tests the broadcast candidate against its own
+// particle with packed FP32x2 arithmetic (no integer work per test) and appends
+// hits to its row, so each row holds its neighbours in (stencil cell, index)
+// order.  Candidates within a relative band of 1e-5 of r_list^2 are decided in
+// FP64 as the definition does (the FP32 error is below 2e-6 relative).
 constexpr float NL_BAND = 1e-5f;
+constexpr int NL_TYPE_SHIFT = 30;
 
-__global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_nlist(const SysDev* __restrict__ sysv,
-                                                               const Tile* __restrict__ tiles,
-                                                               GroupCtl* ctl) {
+// fixed-point coordinate of the centre of cell c of nc along an axis
+__device__ __forceinline__ int cell_centre_fixed(int c, int nc) {
+  const unsigned long long u = ((2ull * (unsigned long long)c + 1ull) << 32) / (2ull * (unsigned long long)nc);
+  return (int)((unsigned int)u ^ 0x80000000u);
+}
+
+// REL: every axis has at least 3 cells, so a candidate's coordinate relative to the
+// cell centre, taken in [-L/2, L/2), is already its minimum image with respect to
+// every particle of the cell (|d| < r_list <= w and the particle lies within w/2
+// of the centre).  With 1 or 2 cells on an axis a neighbour may sit on either side,
+// so the !REL variant keeps fixed-point coordinates and takes the minimum image
+// per test.
+template <bool MULTI, bool REL>
+__global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* __restrict__ sysv,
+                                                                  const Tile* __restrict__ tiles,
+                                                                  GroupCtl* ctl) {
   const Tile t = tiles[blockIdx.x];
   const SysDev& s = sysv[t.sys];
   count(s, t, ctl);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!rebuilding(s) || w >= t.count) return;
   const int nt = s.ntypes;
-  __shared__ float rl2s[CELLS_PER_TILE][MAXT2];
+  // r_list^2 (1 -+ band) per type pair (FP32)
+  __shared__ float thr_lo[CELLS_PER_TILE][MAXT2], thr_hi[CELLS_PER_TILE][MAXT2];
   __shared__ double rl2d[CELLS_PER_TILE][MAXT2];
+  __shared__ float4 cand[CELLS_PER_TILE][32];
   for (int k = lane; k < nt * nt; k += 32) {
-    rl2s[w][k] = s.pf[k].rl2;
+    const float rl2 = s.pf[k].rl2;
+    thr_lo[w][k] = rl2 * (1.0f - NL_BAND);
+    thr_hi[w][k] = rl2 * (1.0f + NL_BAND);
     rl2d[w][k] = s.pd[k].rl2;
   }
-  __syncwarp();
   const int r = t.first + w;
   const int nc0 = s.nc[0], nc1 = s.nc[1], nc2 = s.nc[2];
   const int lin = s.rank2lin[r];
   const int cx = lin % nc0, cy = (lin / nc0) % nc1, cz = lin / (nc0 * nc1);
-  // distinct neighbour-cell offsets per axis (fewer than 3 cells: no duplicates)
-  const int lo0 = nc0 >= 3 ? -1 : 0, hi0 = nc0 >= 3 ? 1 : nc0 - 1;
-  const int lo1 = nc1 >= 3 ? -1 : 0, hi1 = nc1 >= 3 ? 1 : nc1 - 1;
-  const int lo2 = nc2 >= 3 ? -1 : 0, hi2 = nc2 >= 3 ? 1 : nc2 - 1;
+  const int ox = cell_centre_fixed(cx, nc0), oy = cell_centre_fixed(cy, nc1),
+            oz = cell_centre_fixed(cz, nc2);
   const float fs0 = s.fscale[0], fs1 = s.fscale[1], fs2 = s.fscale[2];
+  // distinct neighbour-cell offsets per axis (fewer than 3 cells: no duplicates)
+  const int lo0 = nc0 >= 3 ? -1 : 0, n0 = nc0 >= 3 ? 3 : nc0;
+  const int lo1 = nc1 >= 3 ? -1 : 0, n1 = nc1 >= 3 ? 3 : nc1;
+  const int lo2 = nc2 >= 3 ? -1 : 0, n2 = nc2 >= 3 ? 3 : nc2;
+  const int nsc = n0 * n1 * n2;   // <= 27
+  int sc_start = 0, sc_cnt = 0;
+  if (lane < nsc) {
+    const int dx = lo0 + lane % n0, dy = lo1 + (lane / n0) % n1, dz = lo2 + lane / (n0 * n1);
+    const int x = (cx + dx + nc0) % nc0, y = (cy + dy + nc1) % nc1, z = (cz + dz + nc2) % nc2;
+    const int nr = s.lin2rank[(z * nc1 + y) * nc0 + x];
+    sc_start = s.cell_start[nr];
+    sc_cnt = s.cell_start[nr + 1] - sc_start;
+  }
+  int incl = sc_cnt;   // inclusive prefix of the stencil cells' sizes
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int excl = incl - sc_cnt;
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
   const int b = s.cell_start[r], e = s.cell_start[r + 1];
   const int cap = s.cap;
+  const int* __restrict__ members = s.members;
+  const int4* __restrict__ qv = s.q;
+  __syncwarp();
+
+  // candidate c of the flattened stream, relative to the cell centre; every lane
+  // runs every shuffle
+  auto fetch = [&](int c) -> float4 {
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int mid = lo + step;
+      const int v = __shfl_sync(0xffffffffu, excl, mid & 31);
+      if (mid < nsc && c >= v) lo = mid;
+    }
+    const int st = __shfl_sync(0xffffffffu, sc_start, lo);
+    const int ex = __shfl_sync(0xffffffffu, excl, lo);
+    if (c >= total) return make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    const int j = members[st + (c - ex)];
+    const int4 qj = qv[j];
+    if (!REL)
+      return make_float4(__int_as_float(qj.x), __int_as_float(qj.y), __int_as_float(qj.z),
+                         __int_as_float(j | (qj.w << NL_TYPE_SHIFT)));
+    return make_float4((float)min_image_fixed(qj.x, ox) * fs0, (float)min_image_fixed(qj.y, oy) * fs1,
+                       (float)min_image_fixed(qj.z, oz) * fs2, __int_as_float(j | (qj.w << NL_TYPE_SHIFT)));
+  };
+
   unsigned long long nb_sum = 0;
-  for (int base = b; base < e; base += 32) {
-    const bool valid = base + lane < e;
-    const int i = valid ? s.members[base + lane] : -1;
-    const int4 qi = valid ? s.q[i] : make_int4(0, 0, 0, 0);
-    const int ti = qi.w;
-    int* row = s.nl + (size_t)(valid ? i : 0) * cap;
+  for (int ibase = b; ibase < e; ibase += 32) {
+    const bool valid = ibase + lane < e;
+    const int i = valid ? members[ibase + lane] : -1;
+    const int4 qi = valid ? qv[i] : make_int4(0, 0, 0, 0);
+    const float xi = (float)min_image_fixed(qi.x, ox) * fs0;
+    const float yi = (float)min_image_fixed(qi.y, oy) * fs1;
+    const float zi = (float)min_image_fixed(qi.z, oz) * fs2;
+    const float2 nxy = make_float2(-xi, -yi);
+    // squared list range by candidate type, widened by the relative band: the test
+    // loop keeps every candidate below hi = r_list^2 (1 + band) in a bit mask; the
+    // hits are then appended in order, the ones above r_list^2 (1 - band) after an
+    // FP64 decision.  Two types in registers; more types read the table.  An idle
+    // lane gets -1 (never keeps).
+    const int pt = MULTI ? qi.w * nt : 0;
+    const float hi0 = valid ? thr_hi[w][pt] : -1.0f;
+    const float hi1 = valid && MULTI ? thr_hi[w][pt + min(1, nt - 1)] : hi0;
+    const bool two = !MULTI || nt <= 2;
+    int* __restrict__ nl = s.nl;
+    const int stride = s.nl_stride;
+    const int i_row = valid ? i : 0;
     int cnt = 0;
-    for (int oz = lo2; oz <= hi2; ++oz) {
-      const int z = (cz + oz + nc2) % nc2;
-      for (int oy = lo1; oy <= hi1; ++oy) {
-        const int y = (cy + oy + nc1) % nc1;
-        for (int ox = lo0; ox <= hi0; ++ox) {
-          const int x = (cx + ox + nc0) % nc0;
-          const int nr = s.lin2rank[(z * nc1 + y) * nc0 + x];
-          const int jb = s.cell_start[nr], je = s.cell_start[nr + 1];
-          for (int jj = jb; jj < je; ++jj) {
-            const int j = s.members[jj];
-            const int4 qj = s.q[j];
-            if (!valid || j == i) continue;
-            const float dx = (float)min_image_fixed(qi.x, qj.x) * fs0;
-            const float dy = (float)min_image_fixed(qi.y, qj.y) * fs1;
-            const float dz = (float)min_image_fixed(qi.z, qj.z) * fs2;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const int p = ti * nt + qj.w;
-            const float rl2 = rl2s[w][p];
-            bool keep = r2 < rl2 * (1.0f - NL_BAND);
-            if (!keep && r2 < rl2 * (1.0f + NL_BAND)) keep = exact_within(s, i, j, rl2d[w][p]);
-            if (keep) {
-              if (cnt < cap) row[cnt] = j;
-              ++cnt;
-            }
-          }
+    float4 next = fetch(lane);
+    for (int cb = 0; cb < total; cb += 32) {
+      cand[w][lane] = next;
+      __syncwarp();
+      if (cb + 32 < total) next = fetch(cb + 32 + lane);   // in flight during the tests
+      const int m = min(32, total - cb);
+      unsigned mask = 0;
+      auto test = [&](int k) {
+        const float4 c = cand[w][k];
+        float r2;   // exactly 0 for the particle itself (dropped below)
+        if (REL) {
+          const float2 dxy = __fadd2_rn(make_float2(c.x, c.y), nxy);
+          const float dz = c.z - zi;
+          const float2 sq = __fmul2_rn(dxy, dxy);
+          r2 = fmaf(dz, dz, sq.x + sq.y);
+        } else {
+          const float dx = (float)min_image_fixed(qi.x, __float_as_int(c.x)) * fs0;
+          const float dy = (float)min_image_fixed(qi.y, __float_as_int(c.y)) * fs1;
+          const float dz = (float)min_image_fixed(qi.z, __float_as_int(c.z)) * fs2;
+          r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        }
+        float hi;
+        if (!MULTI) hi = hi0;
+        else if (two) hi = ((__float_as_int(c.w) >> NL_TYPE_SHIFT) & 1) ? hi1 : hi0;
+        else hi = valid ? thr_hi[w][pt + ((unsigned)__float_as_int(c.w) >> NL_TYPE_SHIFT)] : -1.0f;
+        return r2 < hi;
+      };
+      if (m == 32) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) mask |= test(k) ? (1u << k) : 0u;
+      } else {
+        for (int k = 0; k < m; ++k) mask |= test(k) ? (1u << k) : 0u;
+      }
+      while (mask) {   // about a tenth of the candidates
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float4 c = cand[w][k];
+        const int cw = __float_as_int(c.w);
+        const int j = cw & ((1 << NL_TYPE_SHIFT) - 1);
+        if (j == i) continue;
+        float r2;
+        if (REL) {
+          const float2 dxy = __fadd2_rn(make_float2(c.x, c.y), nxy);
+          const float dz = c.z - zi;
+          const float2 sq = __fmul2_rn(dxy, dxy);
+          r2 = fmaf(dz, dz, sq.x + sq.y);
+        } else {
+          const float dx = (float)min_image_fixed(qi.x, __float_as_int(c.x)) * fs0;
+          const float dy = (float)min_image_fixed(qi.y, __float_as_int(c.y)) * fs1;
+          const float dz = (float)min_image_fixed(qi.z, __float_as_int(c.z)) * fs2;
+          r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        }
+        const int p = MULTI ? pt + ((unsigned)cw >> NL_TYPE_SHIFT) : 0;
+        const bool keep = r2 < thr_lo[w][p] || exact_within(s, i, j, rl2d[w][p]);
+        if (keep) {
+          nl[nl_index(i_row, min(cnt, cap - 1), stride)] = j;   // an overflowing row is rebuilt
+          ++cnt;
         }
       }
+      __syncwarp();
     }
     if (valid) {
       s.nn[i] = cnt < cap ? cnt : cap;
@@ -302,7 +422,15 @@ SIMPLE_CALL(scatter_call, k_scatter, TILE_P)
 SIMPLE_CALL(cellsort_call, k_cellsort, CELLS_PER_TILE * 32)
 SIMPLE_CALL(permute_call, k_permute, TILE_P)
 SIMPLE_CALL(copyback_call, k_copyback, TILE_P)
-SIMPLE_CALL(nlist_call, k_nlist, CELLS_PER_TILE * 32)
 #undef SIMPLE_CALL
+
+KernelCall nlist_call(const SysDev* d, const Tile* tl, int ntiles, GroupCtl* ctl, bool rel,
+                      bool multi) {
+  void* f = multi ? (rel ? (void*)k_nlist<true, true> : (void*)k_nlist<true, false>)
+                  : (rel ? (void*)k_nlist<false, true> : (void*)k_nlist<false, false>);
+  KernelCall k = make_call(f, ntiles, CELLS_PER_TILE * 32, 0);
+  put(k, d); put(k, tl); put(k, ctl);
+  return k;
+}
 
 }  // namespace gbmd

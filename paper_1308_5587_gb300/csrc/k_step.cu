@@ -38,56 +38,76 @@ __global__ void __launch_bounds__(TILE_P) k_integrate(const SysDev* __restrict__
   bool need = false, bad = false;
   const int i = t.first + threadIdx.x;
   if (active && threadIdx.x < t.count) {
+    // descriptor fields and every load first (no store may alias them), then math
     const int n = s.n;
+    double* __restrict__ xp = s.x;
+    double* __restrict__ vp = s.v;
+    const double kick = vfull ? s.h : 2.0 * s.h;   // closing + opening half kicks
+    const double dtq[3] = {s.dt * s.qscale[0], s.dt * s.qscale[1], s.dt * s.qscale[2]};
+    const float fsc[3] = {s.fscale[0], s.fscale[1], s.fscale[2]};
+    const double Lr[3] = {s.L[0] * (1.0 / 4294967296.0), s.L[1] * (1.0 / 4294967296.0),
+                          s.L[2] * (1.0 / 4294967296.0)};
+    const float rb2 = s.rbuff_half2;
+    int* __restrict__ imgp = s.img;
+    int4* __restrict__ qp = s.q;
+    double4_32a* __restrict__ p64p = s.p64;
     double f[3];
     if (PREC == GBMD_FP64) {
-      double4_32a F = s.f64[i];
+      const double4_32a F = s.f64[i];
       f[0] = F.x; f[1] = F.y; f[2] = F.z;
     } else {
-      float4 F = s.f32[i];
+      const float4 F = __ldg(s.f32 + i);
       f[0] = F.x; f[1] = F.y; f[2] = F.z;
     }
-    const double kick = vfull ? s.h : 2.0 * s.h;   // closing + opening half kicks
+    double v[3], xq[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      v[a] = vp[a * n + i];
+      xq[a] = xp[a * n + i];
+    }
+    const int ty = __ldg(s.type + i);
+    const int4 qb = __ldg(s.q_build + i);
     int q[3];
     double xr[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double v = s.v[a * n + i];
-      v = fma(kick, f[a], v);
-      s.v[a * n + i] = v;
-      double xq = s.x[a * n + i];
-      xq = fma(s.dt * s.qscale[a], v, xq);
-      long long qq = __double2ll_rn(xq);
-      long long k = (qq + 0x80000000LL) >> 32;       // floor((xq + 2^31) / 2^32)
+      v[a] = fma(kick, f[a], v[a]);
+      xq[a] = fma(dtq[a], v[a], xq[a]);
+      long long qq = __double2ll_rn(xq[a]);
+      const long long k = (qq + 0x80000000LL) >> 32;       // floor((xq + 2^31) / 2^32)
       if (k != 0) {
-        if (k > 1 || k < -1 || !isfinite(xq)) bad = true;
-        xq -= (double)k * 4294967296.0;
+        if (k > 1 || k < -1 || !isfinite(xq[a])) bad = true;
+        xq[a] -= (double)k * 4294967296.0;
         qq -= k << 32;
-        s.img[a * n + i] += (int)k;
+        imgp[a * n + i] += (int)k;
       }
-      s.x[a * n + i] = xq;
       q[a] = (int)qq;
-      xr[a] = xq * (s.L[a] * (1.0 / 4294967296.0));
+      xr[a] = xq[a] * Lr[a];
     }
-    const int ty = s.type[i];
-    s.q[i] = make_int4(q[0], q[1], q[2], ty);
-    if (PREC == GBMD_FP64) s.p64[i] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
-    const int4 qb = s.q_build[i];
-    float dx = (float)min_image_fixed(q[0], qb.x) * s.fscale[0];
-    float dy = (float)min_image_fixed(q[1], qb.y) * s.fscale[1];
-    float dz = (float)min_image_fixed(q[2], qb.z) * s.fscale[2];
-    need = dx * dx + dy * dy + dz * dz > s.rbuff_half2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      vp[a * n + i] = v[a];
+      xp[a * n + i] = xq[a];
+    }
+    qp[i] = make_int4(q[0], q[1], q[2], ty);
+    if (PREC == GBMD_FP64) p64p[i] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
+    const float dx = (float)min_image_fixed(q[0], qb.x) * fsc[0];
+    const float dy = (float)min_image_fixed(q[1], qb.y) * fsc[1];
+    const float dz = (float)min_image_fixed(q[2], qb.z) * fsc[2];
+    need = dx * dx + dy * dy + dz * dz > rb2;
   }
+  if (bad) atomicCAS(&fl->error, 0, (int)DEV_NONFINITE);   // rare: no block reduction
   const int any_need = __syncthreads_or(need);
-  const int any_bad = __syncthreads_or(bad);
-  if (threadIdx.x == 0) {
-    if (any_need) atomicOr(&fl->rebuild_req, 1);
-    if (any_bad) atomicCAS(&fl->error, 0, (int)DEV_NONFINITE);
-  }
 
   // ---- the last block to finish makes the per-step decisions ----
+  // Only thread 0 publishes: its flag update, a fence, then the arrival count
+  // (the position stores of this step need not be visible to the last block).
   __shared__ int last;
-  __threadfence();
-  if (threadIdx.x == 0) last = (atomicAdd(&ctl->blocks_done, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) {
+    if (any_need) atomicOr(&fl->rebuild_req, 1);
+    __threadfence();
+    last = (atomicAdd(&ctl->blocks_done, 1u) == gridDim.x - 1);
+  }
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -282,9 +302,8 @@ __global__ void __launch_bounds__(TILE_P) k_nlist_export(const SysDev* __restric
     return;
   }
   int* out = idx + (size_t)tg * cap_out;
-  const int* row = s.nl + (size_t)i * s.cap;
   for (int k = 0; k < nn; ++k) {   // insertion sort of the tags (rows are short)
-    int v = s.tag[row[k]];
+    int v = s.tag[s.nl[nl_index(i, k, s.nl_stride)]];
     int p = k;
     while (p > 0 && out[p - 1] > v) {
       out[p] = out[p - 1];

@@ -37,7 +37,8 @@ KernelCall scatter_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupC
 KernelCall cellsort_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl* ctl);
 KernelCall permute_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
 KernelCall copyback_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
-KernelCall nlist_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl* ctl);
+KernelCall nlist_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl* ctl, bool rel,
+                      bool multi);
 // pair force (K5): ev = 0 forces only, 1 also energy/virial partial sums
 // (+ per-particle arrays when the descriptor has them); force_all ignores the
 // per-step activity flag (used outside the step graph)

@@ -289,12 +289,12 @@ def test_batch_alone_equals_in_mix(prec):
     alone = []
     for w in ws:
         s = gbmd.System.from_workload(w, precision=prec)
-        s.set_tuning(8, 256)
+        s.set_tuning(2, 256)
         s.step(60)
         alone.append((s.state(), s.forces(), s.thermo()))
         s.close()
     b = gbmd.Batch(prec)
-    b.set_tuning(8, 256)
+    b.set_tuning(2, 256)
     sys_ = [gbmd.System.from_workload(w, precision=prec) for w in ws]
     for s in sys_:
         b.add(s)

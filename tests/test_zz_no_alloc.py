@@ -61,13 +61,13 @@ def test_noalloc_thermo_matches_allocating_thermo(prec):
 
 
 def test_noalloc_thermo_rejects_systems_over_the_limit():
-    w = wl.lj_fluid(70000, 0.84, 1.2, seed=503)
+    w = wl.lj_fluid(270000, 0.84, 1.2, seed=503)
     s = gbmd.System.from_workload(w, precision="mixed")
-    s.set_tuning(32, 64)       # two particles per force tile -> 35,000 tiles > 32,768
+    s.set_tuning(4, 32)        # eight particles per force tile -> 33,750 tiles > 32,768
     with pytest.raises(gbmd.GbmdError) as e:
         gbmd.gbmd_get_thermo_noalloc(s.handle)
     assert e.value.status == "BAD_ARG"
     assert "allocation-free limit" in str(e.value)
-    s.set_tuning(8, 256)
+    s.set_tuning(2, 256)
     _same(gbmd.gbmd_get_thermo_noalloc(s.handle), gbmd.gbmd_get_thermo(s.handle), "mixed")
     s.close()
