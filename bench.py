@@ -298,7 +298,8 @@ def gpu_arm(args):
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     s = gbmd.System.from_workload(w, precision=precision, sort_period=sort_period,
-                                  stream=stream.cuda_stream, cuda_device=local)
+                                  stream=stream.cuda_stream, cuda_device=local,
+                                  force_path=args.force_path)
     if args.autotune:
         s.autotune(os.path.join(ROOT, "_work", "tune_cache.txt") if os.path.isdir(
             os.path.join(ROOT, "_work")) else None)
@@ -329,8 +330,9 @@ def gpu_arm(args):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": recorded_traffic(args.workload, precision),
-                "kernel": f"k_force<{precision}> tpp={info['threads_per_particle']} "
-                          f"block={info['force_block']}",
+                "kernel": (f"k_force_staged<{precision}>" if info["force_path"] == 1 else
+                           f"k_force<{precision}> tpp={info['threads_per_particle']} "
+                           f"block={info['force_block']}"),
                 "alg_bytes_per_launch": int(alg_bytes), "mean_neighbors": round(nbar, 2),
                 "force_ms_mean": round(f_mean, 5), "peak_kind": f"of {peak_kind}",
                 "force_share_of_step": round(f_mean / float(step_ms.mean()), 3)}
@@ -349,6 +351,7 @@ def gpu_arm(args):
                                                             "one single-step CUDA graph") + ")",
                       "threads_per_particle": info["threads_per_particle"],
                       "force_block": info["force_block"], "nlist_capacity": info["nlist_capacity"],
+                      "force_path": "staged" if info["force_path"] == 1 else "global",
                       "sort_period": sort_period},
            "tps": args.steps / t_max, "roofline": roofline, "clocks": clk,
            "gpu_launches": int(launches),
@@ -452,6 +455,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gbmd", "reference"], default="gbmd")
     ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k"], default="lj64k")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--force-path", choices=["global", "staged"], default="global",
+                    help="neighbour gather through L1/L2 by 32-bit index (default) or "
+                         "from a shared-memory window by 16-bit index")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define GBMD_ABI_VERSION 1
+#define GBMD_ABI_VERSION 2
 #define GBMD_MAX_TYPES 4
 
 typedef enum gbmd_status {
@@ -88,11 +88,23 @@ typedef struct gbmd_desc {
                                    0 = sort only when the system is created */
     int32_t nlist_capacity;     /* neighbours per particle to reserve; 0 = from density */
     int32_t threads_per_particle; /* lanes per particle in the force kernel:
-                                     0 = default (2); else 1, 2 or 4 */
+                                     0 = default (1 from 2^19 particles up, else 2);
+                                     else 1, 2 or 4 */
     void *stream;               /* cudaStream_t to run on; NULL = the legacy default stream */
     int32_t device;             /* CUDA device ordinal; -1 = the calling thread's current
                                    device.  Every later call on the system uses it. */
+    int32_t force_path;         /* GBMD_PATH_GLOBAL (0, default): the force kernel gathers
+                                   neighbour positions through L1/L2 by 32-bit index.
+                                   GBMD_PATH_STAGED (1): mixed precision only; each block
+                                   of 2x2x2 cells stages its 4x4x4-cell window in shared
+                                   memory and the list holds 16-bit window indices.  Used
+                                   only where every cell axis has >= 4 cells and the
+                                   expected window fits; a window that outgrows shared
+                                   memory at a rebuild switches the system to the global
+                                   path for good.  gbmd_get_info reports the path in use. */
 } gbmd_desc;
+
+enum { GBMD_PATH_GLOBAL = 0, GBMD_PATH_STAGED = 1 };
 
 /* Thermodynamic quantities of one system at its current step (FP64). */
 typedef struct gbmd_thermo {
@@ -122,6 +134,10 @@ typedef struct gbmd_info {
                                      (counted on the device) */
     int64_t neighbors_total;      /* sum of neighbour counts at the last build */
     int64_t footprint_bytes;      /* device memory held */
+    int32_t force_path;           /* 0: global neighbour indices; 1: staged windows (2x2x2
+                                     cell blocks with their 4x4x4-cell neighbourhood in
+                                     shared memory, 16-bit window-local indices) */
+    int32_t max_window;           /* largest staged window at the last build (particles) */
 } gbmd_info;
 
 typedef struct gbmd_system gbmd_system;
@@ -168,9 +184,10 @@ int gbmd_get_thermo(gbmd_system *s, gbmd_thermo *out);
  * device arrays of this library (2 MiB + one descriptor, held on every device
  * that loads the library until the process exits) instead of in buffers the
  * library allocates.  Limits and behaviour:
- *   - systems with more than GBMD_NOALLOC_MAX_TILES force-kernel tiles (one tile
- *     = force block / threads per particle particles, 128 at the default tuning,
- *     so about four million particles) are rejected with GBMD_ERR_BAD_ARG;
+ *   - systems with more than GBMD_NOALLOC_MAX_TILES energy tiles are rejected
+ *     with GBMD_ERR_BAD_ARG: one tile is 128 particles on the global force path
+ *     (so at most 4,194,304 particles) and one 2x2x2 block of cells on the
+ *     staged path;
  *   - the first call on a device looks up the static arrays' device addresses
  *     (cudaGetSymbolAddress), once; make that first call before any stream
  *     capture begins;

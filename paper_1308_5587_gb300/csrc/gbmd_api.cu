@@ -52,6 +52,7 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 constexpr int STEPS_PER_GRAPH = 16;
+constexpr int STAGED_WINDOW_CAP = 3072;   // window particles in 48 KB of shared memory
 
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
@@ -83,15 +84,20 @@ struct Group {
   std::vector<gbmd_system*> members;   // may contain nullptr (free slots of a batch)
   bool is_batch = false;
   int precision = GBMD_MIXED;
-  int multi = 0;
+  int multi = 0;   // pair-table mode: 0 one type, 1 at most two, 2 more
   bool rel = true;     // every member has at least 3 cells on every axis
   cudaStream_t stream = nullptr;
-  int tpp = 2, fblock = 256;
+  int tpp = 2, fblock = 128;
   // device tables
   SysDev* d_desc = nullptr;
   Tile *d_tp = nullptr, *d_tf = nullptr, *d_tc = nullptr, *d_ts = nullptr;
-  int ntp = 0, ntf = 0, ntc = 0, nts = 0;
+  Tile *d_tb = nullptr, *d_tbk = nullptr;   // staged force blocks; their window kernel
+  Tile* d_te = nullptr;   // energy/virial launches: EV_TILE_P particles per tile, whatever
+                          // the tuning, so the FP64 sums do not depend on it
+  int ntp = 0, ntf = 0, ntc = 0, nts = 0, ntb = 0, ntbk = 0, nte = 0;
   size_t cap_desc = 0, cap_tp = 0, cap_tf = 0, cap_tc = 0, cap_ts = 0, cap_part = 0;
+  size_t cap_tb = 0, cap_tbk = 0, cap_te = 0;
+  int window_cap = 0;                        // largest staged window among members
   double* d_partials = nullptr;
   GroupCtl* d_ctl = nullptr;
   cudaGraphExec_t exec_many = nullptr, exec_one = nullptr;
@@ -147,45 +153,70 @@ int sync_layout(Group* g) {
   if (!g->layout_dirty) return GBMD_OK;
   std::vector<gbmd_system*> m = live(g);
   std::vector<SysDev> desc;
-  std::vector<Tile> tp, tf, tc, ts;
+  std::vector<Tile> tp, tf, tc, ts, tb, tbk, te;
   const int per_f = g->fblock / g->tpp;
   g->multi = 0;
   g->rel = true;
+  g->window_cap = 0;
   for (size_t k = 0; k < m.size(); ++k) {
     SysDev d = m[k]->h;
     const int n = d.n;
     for (int f = 0; f < n; f += TILE_P) tp.push_back({(int)k, f, std::min(TILE_P, n - f), 0});
-    d.tile_first_f = (int)tf.size();
-    for (int f = 0; f < n; f += per_f) tf.push_back({(int)k, f, std::min(per_f, n - f), 0});
-    d.tile_count_f = (int)tf.size() - d.tile_first_f;
+    if (d.staged) {   // one force tile per 2x2x2 block of cells
+      d.tile_first_f = (int)tb.size();   // shifted past the global tiles below
+      for (int b = 0; b < d.nblocks; ++b) tb.push_back({(int)k, b, 1, 0});
+      d.tile_count_f = d.nblocks;
+      for (int b = 0; b < d.nblocks; b += 8) tbk.push_back({(int)k, b, std::min(8, d.nblocks - b), 0});
+      g->window_cap = std::max(g->window_cap, d.window_cap);
+    } else {
+      for (int f = 0; f < n; f += per_f) tf.push_back({(int)k, f, std::min(per_f, n - f), 0});
+      d.tile_first_f = (int)te.size();   // partial sums come from the energy launches
+      for (int f = 0; f < n; f += EV_TILE_P) te.push_back({(int)k, f, std::min(EV_TILE_P, n - f), 0});
+      d.tile_count_f = (int)te.size() - d.tile_first_f;
+    }
     for (int c = 0; c < d.ncells; c += CELLS_PER_TILE)
       tc.push_back({(int)k, c, std::min(CELLS_PER_TILE, d.ncells - c), 0});
     ts.push_back({(int)k, 0, 0, 0});
     desc.push_back(d);
-    if (d.ntypes > 1) g->multi = 1;
+    if (d.ntypes > 1) g->multi = std::max(g->multi, d.ntypes > 2 ? 2 : 1);
     if (d.nc[0] < 3 || d.nc[1] < 3 || d.nc[2] < 3) g->rel = false;
   }
-  RET(grow(&g->d_partials, &g->cap_part, 8 * std::max<size_t>(tf.size(), 1)));
+  for (auto& d : desc)
+    if (d.staged) d.tile_first_f += (int)te.size();   // staged partial sums follow the global ones
+  RET(grow(&g->d_partials, &g->cap_part, 8 * std::max<size_t>(te.size() + tb.size(), 1)));
   for (auto& d : desc) d.partials = g->d_partials;
   RET(grow(&g->d_desc, &g->cap_desc, desc.size()));
   RET(grow(&g->d_tp, &g->cap_tp, tp.size()));
   RET(grow(&g->d_tf, &g->cap_tf, tf.size()));
   RET(grow(&g->d_tc, &g->cap_tc, tc.size()));
   RET(grow(&g->d_ts, &g->cap_ts, ts.size()));
+  RET(grow(&g->d_tb, &g->cap_tb, tb.size()));
+  RET(grow(&g->d_tbk, &g->cap_tbk, tbk.size()));
+  RET(grow(&g->d_te, &g->cap_te, te.size()));
   if (!g->d_ctl) {
     CK(cudaMalloc(&g->d_ctl, sizeof(GroupCtl)));
     CK(cudaMemsetAsync(g->d_ctl, 0, sizeof(GroupCtl), g->stream));
   }
+  auto up = [&](void* dst, const std::vector<Tile>& v) -> cudaError_t {
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice, g->stream);
+  };
   if (!desc.empty()) CK(cudaMemcpyAsync(g->d_desc, desc.data(), desc.size() * sizeof(SysDev), cudaMemcpyHostToDevice, g->stream));
-  if (!tp.empty()) CK(cudaMemcpyAsync(g->d_tp, tp.data(), tp.size() * sizeof(Tile), cudaMemcpyHostToDevice, g->stream));
-  if (!tf.empty()) CK(cudaMemcpyAsync(g->d_tf, tf.data(), tf.size() * sizeof(Tile), cudaMemcpyHostToDevice, g->stream));
-  if (!tc.empty()) CK(cudaMemcpyAsync(g->d_tc, tc.data(), tc.size() * sizeof(Tile), cudaMemcpyHostToDevice, g->stream));
-  if (!ts.empty()) CK(cudaMemcpyAsync(g->d_ts, ts.data(), ts.size() * sizeof(Tile), cudaMemcpyHostToDevice, g->stream));
+  CK(up(g->d_tp, tp));
+  CK(up(g->d_tf, tf));
+  CK(up(g->d_tc, tc));
+  CK(up(g->d_ts, ts));
+  CK(up(g->d_tb, tb));
+  CK(up(g->d_tbk, tbk));
+  CK(up(g->d_te, te));
   CK(cudaStreamSynchronize(g->stream));   // host vectors die here
   g->ntp = (int)tp.size();
   g->ntf = (int)tf.size();
   g->ntc = (int)tc.size();
   g->nts = (int)ts.size();
+  g->ntb = (int)tb.size();
+  g->ntbk = (int)tbk.size();
+  g->nte = (int)te.size();
   g->layout_dirty = false;
   destroy_graphs(g);
   return GBMD_OK;
@@ -202,18 +233,45 @@ int refresh_desc(gbmd_system* s) {
 }
 
 std::vector<KernelCall> rebuild_calls(const Group* g) {
+  if (g->ntbk == 0)
+    return {bin_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+            scan_call(g->d_desc, g->d_ts, g->nts, g->d_ctl),
+            scatter_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+            cellsort_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl),
+            permute_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+            copyback_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+            nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi)};
   return {bin_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
           scan_call(g->d_desc, g->d_ts, g->nts, g->d_ctl),
           scatter_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
           cellsort_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl),
           permute_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
           copyback_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+          blocks_call(g->d_desc, g->d_tbk, g->ntbk, g->d_ctl),
           nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi)};
 }
 
 KernelCall step_force_call(const Group* g, int ev, int force_all) {
   return force_call(g->precision, g->multi, ev, g->tpp, g->fblock, g->d_desc, g->d_tf, g->ntf,
                     g->d_ctl, force_all);
+}
+
+// energy/virial launch of the global-list systems: the step's threads per particle
+// (so the FP32 forces it writes are bitwise the step's), EV_TILE_P particles per block
+KernelCall ev_force_call(const Group* g, const SysDev* desc, int force_all) {
+  return force_call(g->precision, g->multi, 1, g->tpp, EV_TILE_P * g->tpp, desc, g->d_te, g->nte,
+                    g->d_ctl, force_all);
+}
+
+// the force launches of a step (ev = 0) or of a readout (ev = 1): global-list
+// systems, then staged ones
+std::vector<KernelCall> force_calls(const Group* g, int ev, int force_all) {
+  std::vector<KernelCall> v;
+  if (g->ntf > 0) v.push_back(ev ? ev_force_call(g, g->d_desc, force_all) : step_force_call(g, 0, force_all));
+  if (g->ntb > 0)
+    v.push_back(force_staged_call(g->multi, ev, g->d_desc, g->d_tb, g->ntb, g->d_ctl, force_all,
+                                  g->nte, g->window_cap));
+  return v;
 }
 
 int add_kernel(cudaGraph_t graph, const cudaGraphNode_t* dep, const KernelCall& k,
@@ -268,10 +326,15 @@ int build_graph(Group* g, int nsteps, cudaGraphExec_t* exec) {
       if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "event node: %s", cudaGetErrorString(e)); break; }
       before = g->node_ev_begin;
     }
-    rc = add_kernel(graph, &before, step_force_call(g, 0, 0), &n5);
-    prev = n5;
-    if (rc == GBMD_OK && events) {
-      e = cudaGraphAddEventRecordNode(&g->node_ev_end, graph, &n5, 1, g->ev_end);
+    for (const KernelCall& k : force_calls(g, 0, 0)) {
+      rc = add_kernel(graph, &before, k, &n5);
+      if (rc) break;
+      before = n5;
+    }
+    if (rc) break;
+    prev = before;
+    if (events) {
+      e = cudaGraphAddEventRecordNode(&g->node_ev_end, graph, &before, 1, g->ev_end);
       if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "event node: %s", cudaGetErrorString(e)); break; }
       prev = g->node_ev_end;
     }
@@ -310,7 +373,7 @@ int enqueue_steps(Group* g, long long n) {
     for (const KernelCall& c : rebuild_calls(g)) CK(launch(c, g->stream));
     const bool events = n == 1 && g->ev_begin && g->ev_end;
     if (events) CK(cudaEventRecord(g->ev_begin, g->stream));
-    CK(launch(step_force_call(g, 0, 0), g->stream));
+    for (const KernelCall& c : force_calls(g, 0, 0)) CK(launch(c, g->stream));
     if (events) CK(cudaEventRecord(g->ev_end, g->stream));
   }
   return GBMD_OK;
@@ -335,7 +398,7 @@ int rebuild_and_force(gbmd_system* s, int ev) {
   Group* g = s->own;
   RET(sync_layout(g));
   for (const KernelCall& c : rebuild_calls(g)) CK(launch(c, g->stream));
-  CK(launch(step_force_call(g, ev, 1), g->stream));
+  for (const KernelCall& c : force_calls(g, ev, 1)) CK(launch(c, g->stream));
   return GBMD_OK;
 }
 
@@ -373,6 +436,15 @@ int sync_system(gbmd_system* s) {
     RET(read_flags(s, &f, st));
     if (f.error == DEV_NONFINITE)
       return fail(GBMD_ERR_NONFINITE, "non-finite coordinate or a particle moved more than L/2 in one step (step %lld)", f.step);
+    if (f.error == DEV_WINDOW) {   // a staged window outgrew shared memory
+      s->h.staged = 0;
+      RET(refresh_desc(s));
+      f.error = 0;
+      f.do_rebuild = 1;
+      RET(write_flags(s, &f, st));
+      RET(rebuild_and_force(s, 0));
+      continue;
+    }
     if (f.error == DEV_OVERFLOW) {
       RET(grow_nlist(s, std::max(f.overflow_need, s->h.cap + 1)));
       f.error = 0;
@@ -408,6 +480,8 @@ int validate(const gbmd_desc* d, bool device) {
   if (d->sort_period < 0 || d->nlist_capacity < 0) return fail(GBMD_ERR_BAD_ARG, "sort_period and nlist_capacity must be >= 0");
   if (d->threads_per_particle != 0 && !tpp_supported(d->threads_per_particle))
     return fail(GBMD_ERR_BAD_ARG, "threads_per_particle must be 0, 1, 2 or 4");
+  if (d->force_path != GBMD_PATH_GLOBAL && d->force_path != GBMD_PATH_STAGED)
+    return fail(GBMD_ERR_BAD_ARG, "force_path must be GBMD_PATH_GLOBAL or GBMD_PATH_STAGED");
   const int nt = d->ntypes;
   double rmax = 0;
   for (int a = 0; a < nt; ++a)
@@ -482,7 +556,9 @@ size_t footprint_of(const gbmd_desc* d, const Geometry& g) {
   b += n * 32;                   // p64
   b += n * (d->precision == GBMD_FP64 ? 32 : 16);   // force
   b += n * 4 + round_up(n, 32) * 4 * (size_t)g.cap;  // nn, nl (ELL4)
-  b += n * 4 * 3 + (size_t)(g.ncells + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;  // cells
+  b += n * 4 * 4 + (size_t)(g.ncells + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;  // cells
+  b += (size_t)((g.nc[0] + 1) / 2) * ((g.nc[1] + 1) / 2) * ((g.nc[2] + 1) / 2) *
+       (WIN_CELLS * 8 + 16);                                                      // staged blocks
   b += n * (8 * 3 * 2 + 4 * 3 + 4 * 2 + 16);         // re-sort scratch
   b += n * (8 * 3 * 3 + 4 * 3 + 4 * 2);              // import/export staging
   b += 4096;
@@ -515,6 +591,19 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   h.mass = d->mass;
   h.h = 0.5 * d->dt / d->mass;
   h.ncells = geo.ncells;
+  h.nblocks = 1;
+  for (int a = 0; a < 3; ++a) {
+    h.nb[a] = (geo.nc[a] + 1) / 2;
+    h.nblocks *= h.nb[a];
+  }
+  // staged force path: mixed precision, >= 4 cells per axis, expected windows well
+  // inside shared memory (a larger one at a rebuild falls back, see sync_system)
+  {
+    const double per_cell = (double)n / geo.ncells;
+    h.staged = d->force_path == GBMD_PATH_STAGED && d->precision == GBMD_MIXED && geo.nc[0] >= 4 && geo.nc[1] >= 4 &&
+               geo.nc[2] >= 4 && WIN_CELLS * per_cell * 1.35 + 96 <= STAGED_WINDOW_CAP;
+    h.window_cap = STAGED_WINDOW_CAP;
+  }
   for (int a = 0; a < 3; ++a) {
     h.L[a] = d->box[a];
     h.halfL[a] = 0.5 * d->box[a];
@@ -559,6 +648,9 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   if (d->precision == GBMD_FP64) A((void**)&h.f64, N * 32); else A((void**)&h.f32, N * 16);
   A((void**)&h.nn, N * 4); A((void**)&h.nl, round_up(N, 32) * 4 * (size_t)geo.cap);
   A((void**)&h.key, N * 4); A((void**)&h.members, N * 4); A((void**)&h.members_tmp, N * 4);
+  A((void**)&h.rmember, N * 4);
+  A((void**)&h.blk_win, (size_t)h.nblocks * WIN_CELLS * sizeof(int2));
+  A((void**)&h.blk_info, (size_t)h.nblocks * sizeof(int4));
   A((void**)&h.cell_cnt, (geo.ncells + 1) * 4); A((void**)&h.cell_start, (geo.ncells + 1) * 4);
   A((void**)&h.cell_cursor, (geo.ncells + 1) * 4);
   int *r2l = nullptr, *l2r = nullptr;
@@ -603,7 +695,11 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   s->own->stream = st;
   s->own->precision = d->precision;
   s->own->members.push_back(s);
-  if (d->threads_per_particle) s->own->tpp = d->threads_per_particle;
+  // default tuning (measured on GB300 with the L2 flushed between steps): one lane
+  // per particle once there are enough particles to fill every SM several times
+  // over, two below that; 128-thread blocks
+  s->own->tpp = d->threads_per_particle ? d->threads_per_particle : (d->n >= (1 << 19) ? 1 : 2);
+  s->own->fblock = 128;
   if (const char* ev = getenv("GBMD_NO_GRAPHS")) s->own->use_graphs = ev[0] != '1';
   *out = s;
   return GBMD_OK;
@@ -655,6 +751,15 @@ int load_state(gbmd_system* s, const double* pos, const double* vel, const int32
   CK(cudaStreamSynchronize(st));
   Flags after;
   RET(read_flags(s, &after, st));
+  if (after.error == DEV_WINDOW) {
+    s->h.staged = 0;
+    RET(refresh_desc(s));
+    after.error = 0;
+    after.do_rebuild = 1;
+    RET(write_flags(s, &after, st));
+    RET(rebuild_and_force(s, 0));
+    RET(read_flags(s, &after, st));
+  }
   if (after.error == DEV_OVERFLOW) {
     RET(grow_nlist(s, after.overflow_need));
     after.error = 0;
@@ -672,7 +777,7 @@ int thermo_impl(gbmd_system* s, double out[8]) {
   Group* g = s->own;
   RET(sync_layout(g));
   cudaStream_t st = cur_stream(s);
-  CK(launch(step_force_call(g, 1, 1), st));
+  for (const KernelCall& c : force_calls(g, 1, 1)) CK(launch(c, st));
   CK(launch(thermo_call(g->d_desc, g->d_ts, g->nts, g->d_ctl), st));
   CK(cudaMemcpyAsync(out, s->d_thermo, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -702,6 +807,10 @@ int export_impl(gbmd_system* s, double* pos, double* vel, int32_t* image, double
 
 int time_force(Group* g, float* ms) {
   RET(sync_layout(g));
+  if (g->ntf == 0) {
+    *ms = 0.f;
+    return GBMD_OK;
+  }
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
@@ -753,6 +862,7 @@ int set_tuning(Group* g, int tpp, int block) {
 
 int autotune_group(Group* g, const char* cache) {
   RET(sync_layout(g));
+  if (g->ntf == 0) return GBMD_OK;   // every member on the staged path (nothing to tune)
   const std::string key = tune_key(g);
   if (cache) {
     std::ifstream in(cache);
@@ -834,8 +944,9 @@ int gbmd_destroy(gbmd_system* s) {
   if (s->own) {
     Group* g = s->own;
     destroy_graphs(g);
-    cudaFree(g->d_desc); cudaFree(g->d_tp); cudaFree(g->d_tf); cudaFree(g->d_tc);
-    cudaFree(g->d_ts); cudaFree(g->d_partials); cudaFree(g->d_ctl);
+    cudaFree(g->d_desc); cudaFree(g->d_tp); cudaFree(g->d_tf); cudaFree(g->d_tc); cudaFree(g->d_te);
+    cudaFree(g->d_ts); cudaFree(g->d_tb); cudaFree(g->d_tbk); cudaFree(g->d_partials);
+    cudaFree(g->d_ctl);
     delete g;
   }
   delete s;
@@ -984,6 +1095,8 @@ int gbmd_get_info(gbmd_system* s, gbmd_info* out) {
   out->kernel_launches = (int64_t)f.launches;
   out->neighbors_total = (int64_t)f.nb_total;
   out->footprint_bytes = (int64_t)s->footprint;
+  out->force_path = s->h.staged ? 1 : 0;
+  out->max_window = f.max_window;
   return GBMD_OK;
 }
 
@@ -1173,8 +1286,9 @@ int gbmd_batch_destroy(gbmd_batch* bh) {
     s->own->stream = s->stream;
   }
   destroy_graphs(b);
-  cudaFree(b->d_desc); cudaFree(b->d_tp); cudaFree(b->d_tf); cudaFree(b->d_tc);
-  cudaFree(b->d_ts); cudaFree(b->d_partials); cudaFree(b->d_ctl);
+  cudaFree(b->d_desc); cudaFree(b->d_tp); cudaFree(b->d_tf); cudaFree(b->d_tc); cudaFree(b->d_te);
+  cudaFree(b->d_ts); cudaFree(b->d_tb); cudaFree(b->d_tbk); cudaFree(b->d_partials);
+  cudaFree(b->d_ctl);
   delete b;
   return GBMD_OK;
 }
@@ -1244,16 +1358,19 @@ extern "C" int gbmd_get_thermo_noalloc(gbmd_system* s, gbmd_thermo* out) {
   if (s->step_limit >= 0) want = std::min(want, s->step_limit);
   if (f.step < want) return fail(GBMD_ERR_STATE, "steps still owed after a recovery: call gbmd_sync first");
   if (g->layout_dirty) return fail(GBMD_ERR_STATE, "layout changed: call gbmd_sync or gbmd_get_thermo first");
-  if (g->ntf > kNoallocMaxTiles)
-    return fail(GBMD_ERR_BAD_ARG, "%d force tiles exceed the allocation-free limit of %d", g->ntf, kNoallocMaxTiles);
+  if (g->nte + g->ntb > kNoallocMaxTiles)
+    return fail(GBMD_ERR_BAD_ARG, "%d energy tiles exceed the allocation-free limit of %d",
+                g->nte + g->ntb, kNoallocMaxTiles);
   // the system's descriptor, pointed at the static partials (own group: tiles from 0)
   SysDev d = s->h;
   d.tile_first_f = 0;
-  d.tile_count_f = g->ntf;
+  d.tile_count_f = g->nte + g->ntb;   // the system alone: one of the two is zero
   d.partials = addr.partials;
   CK(cudaMemcpyAsync(addr.desc, &d, sizeof(SysDev), cudaMemcpyHostToDevice, st));
-  CK(launch(force_call(g->precision, g->multi, 1, g->tpp, g->fblock, addr.desc, g->d_tf, g->ntf,
-                       g->d_ctl, 1), st));
+  if (g->ntf > 0) CK(launch(ev_force_call(g, addr.desc, 1), st));
+  if (g->ntb > 0)
+    CK(launch(force_staged_call(g->multi, 1, addr.desc, g->d_tb, g->ntb, g->d_ctl, 1, 0,
+                                g->window_cap), st));
   CK(launch(thermo_call(addr.desc, g->d_ts, g->nts, g->d_ctl), st));
   double t[8];
   CK(cudaMemcpyAsync(t, s->d_thermo, sizeof(t), cudaMemcpyDeviceToHost, st));

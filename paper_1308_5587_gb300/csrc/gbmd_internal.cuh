@@ -32,7 +32,11 @@ constexpr int MAXT = GBMD_MAX_TYPES;
 constexpr int MAXT2 = MAXT * MAXT;
 
 // error codes stored in Flags::error (positive on the device)
-enum DevError : int { DEV_OK = 0, DEV_OVERFLOW = 1, DEV_NONFINITE = 2, DEV_BADTYPE = 3 };
+enum DevError : int { DEV_OK = 0, DEV_OVERFLOW = 1, DEV_NONFINITE = 2, DEV_BADTYPE = 3, DEV_WINDOW = 4 };
+
+// staged force tiles: aligned 2x2x2 blocks of cells; their 4x4x4-cell window is
+// staged in shared memory (at most window_cap particles)
+constexpr int WIN_CELLS = 64;
 
 struct Flags {
   int rebuild_req;          // set by the integrate kernel when r_buff/2 is exceeded
@@ -42,7 +46,7 @@ struct Flags {
   int error;                // DevError; nonzero freezes the system
   int overflow_need;        // largest neighbour count seen in an overflowing build
   int v_full;               // 1: v holds full-step velocities (after create / set_state)
-  int pad0;
+  int max_window;           // largest staged window of the last build (particles)
   long long step;           // steps completed
   long long step_limit;     // -1 = none
   long long last_sort;      // step of the last Morton re-sort
@@ -66,7 +70,15 @@ struct SysDev {
   int nc[3];               // cells per axis
   int ncells;
   int n, ntypes, cap, precision;
-  int nl_stride;           // particles per slot group of the ELL4 list (N rounded up to 32)
+  int nl_stride;           // particles per slot group of the list (N rounded up to 32)
+  // staged force path (mixed precision, >= 4 cells per axis): the list holds 16-bit
+  // window-local indices in ELL8 layout, indexed by member rank (cell order)
+  int staged;
+  int nb[3], nblocks;      // 2x2x2 cell blocks per axis, total
+  int window_cap;          // window particles that fit the staged kernel's shared memory
+  int2 *blk_win;           // [nblocks][64]: (member start, window offset) per window cell
+  int4 *blk_info;          // [nblocks]: (first member, particles, window total, 0)
+  int *rmember;            // particle index -> member rank
   int sort_period;
   double dt, h;            // h = dt / (2 m)
   double mass;
@@ -124,6 +136,11 @@ __device__ __forceinline__ int min_image_fixed(int a, int b) {
 // address of entry k of particle i in the ELL4 neighbour list
 __device__ __forceinline__ size_t nl_index(int i, int k, int stride) {
   return ((size_t)(k >> 2) * (size_t)stride + (size_t)i) * 4 + (size_t)(k & 3);
+}
+
+// address of entry k of member m in the staged (ELL8, 16-bit) neighbour list
+__device__ __forceinline__ size_t nl16_index(int m, int k, int stride) {
+  return ((size_t)(k >> 3) * (size_t)stride + (size_t)m) * 8 + (size_t)(k & 7);
 }
 
 // cell coordinate of a fixed-point coordinate: floor((q + 2^31) * nc / 2^32)

@@ -110,7 +110,7 @@ __device__ __forceinline__ void pair2(const int4& qi, const int4& qa, const int4
   }
 }
 
-template <int PREC, int TPP, bool MULTI, bool EV>
+template <int PREC, int TPP, int MT, bool EV>
 __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
                                                const Tile* __restrict__ tiles, GroupCtl* ctl,
                                                int force_all) {
@@ -123,9 +123,10 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
     if (!vf->active || vf->error) return;   // uniform over the block
   }
   const int nt = s.ntypes;
-  __shared__ PairF tabf[MULTI ? MAXT2 : 1];
-  __shared__ PairD tabd[MULTI ? MAXT2 : 1];
-  if (MULTI) {
+  constexpr bool SMEM_TAB = PREC == GBMD_MIXED ? MT == 2 : MT != 0;
+  __shared__ PairF tabf[SMEM_TAB ? MAXT2 : 1];
+  __shared__ PairD tabd[SMEM_TAB ? MAXT2 : 1];
+  if (SMEM_TAB) {
     for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
       if (PREC == GBMD_MIXED) tabf[k] = s.pf[k]; else tabd[k] = s.pd[k];
     }
@@ -148,6 +149,15 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
     const float2 sc1 = make_float2(s.fscale[1], s.fscale[1]);
     const float2 sc2 = make_float2(s.fscale[2], s.fscale[2]);
     const PairF p0 = s.pf[0];
+    // two types: particle i's row of the pair table stays in registers, so a
+    // neighbour's parameters are a select, not a shared-memory load per pair
+    const PairF r0 = MT == 1 ? s.pf[qi.w * nt] : p0;
+    const PairF r1 = MT == 1 ? s.pf[qi.w * nt + nt - 1] : p0;
+    auto par = [&](int tj) -> PairF {
+      if (MT == 0) return p0;
+      if (MT == 1) return tj ? r1 : r0;
+      return tabf[qi.w * nt + tj];
+    };
     const int4* __restrict__ qv = s.q;
     float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx, e = fx;
     float2 w[6] = {fx, fx, fx, fx, fx, fx};
@@ -160,10 +170,7 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
       const int4 q1 = __ldg(qv + (o1 ? jc.y : i));
       const int4 q2 = __ldg(qv + (o2 ? jc.z : i));
       const int4 q3 = __ldg(qv + (o3 ? jc.w : i));
-      const PairF P0 = MULTI ? tabf[qi.w * nt + q0.w] : p0;
-      const PairF P1 = MULTI ? tabf[qi.w * nt + q1.w] : p0;
-      const PairF P2 = MULTI ? tabf[qi.w * nt + q2.w] : p0;
-      const PairF P3 = MULTI ? tabf[qi.w * nt + q3.w] : p0;
+      const PairF P0 = par(q0.w), P1 = par(q1.w), P2 = par(q2.w), P3 = par(q3.w);
       pair2<EV>(qi, q0, q1, o0, o1, sc0, sc1, sc2, P0, P1, fx, fy, fz, e, w);
       pair2<EV>(qi, q2, q3, o2, o3, sc0, sc1, sc2, P2, P3, fx, fy, fz, e, w);
     }
@@ -214,7 +221,7 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
         if ((__double2hiint(dy) & 0x7fffffff) > h1) dy -= copysign(L1, dy);
         if ((__double2hiint(dz) & 0x7fffffff) > h2) dz -= copysign(L2, dz);
         const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        const PairD P = MULTI ? tabd[ti * nt + (int)__double_as_longlong(pj.w)] : p0;
+        const PairD P = MT ? tabd[ti * nt + (int)__double_as_longlong(pj.w)] : p0;
         // both positive, so the bit patterns order like the values
         const bool in = k0 + u < n && __double_as_longlong(r2) < __double_as_longlong(P.rc2);
         if (in) {
@@ -258,28 +265,184 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
   }
 }
 
-bool tpp_supported(int tpp) { return tpp == 1 || tpp == 2 || tpp == 4; }
-
-template <int PREC, int TPP>
-static void* pick3(int multi, int ev) {
-  if (multi) return ev ? (void*)k_force<PREC, TPP, true, true> : (void*)k_force<PREC, TPP, true, false>;
-  return ev ? (void*)k_force<PREC, TPP, false, true> : (void*)k_force<PREC, TPP, false, false>;
-}
-
-template <int PREC>
-static void* pick2(int tpp, int multi, int ev) {
-  switch (tpp) {
-    case 1: return pick3<PREC, 1>(multi, ev);
-    case 2: return pick3<PREC, 2>(multi, ev);
-    default: return pick3<PREC, 4>(multi, ev);
+// ---- staged path: one kernel block per aligned 2x2x2 block of cells ----------------
+// The block's window (the 4x4x4 cells around it, at most window_cap particles) is
+// copied into shared memory as three int arrays (x, y, z with the type in z's two
+// low bits): random 4-byte reads conflict far less across banks than 16-byte ones.
+// Its particles' lists hold 16-bit window-local indices (ELL8: one int4 = 8 entries
+// of one member), so every neighbour position comes from shared memory and the
+// index stream is half as long.  One thread per particle.
+template <int MT, bool EV>
+__global__ void __launch_bounds__(STAGED_BLOCK) k_force_staged(const SysDev* __restrict__ sysv,
+                                                               const Tile* __restrict__ tiles,
+                                                               GroupCtl* ctl, int force_all,
+                                                               int part_base) {
+  extern __shared__ int wsm[];   // window as three int arrays: x, y, z | type
+  const Tile t = tiles[blockIdx.x];
+  const SysDev& s = sysv[t.sys];
+  if (threadIdx.x == 0 && t.first == 0) atomicAdd(&s.flags->launches, 1ull);
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
+  {
+    const volatile Flags* vf = s.flags;
+    if (vf->error) return;                  // e.g. a window too large: nothing is valid
+    if (!force_all && !vf->active) return;  // uniform over the block
+  }
+  const int b = t.first;
+  const int4 info = s.blk_info[b];          // (first member, particles, window total, 0)
+  if (info.z > s.window_cap) return;        // never index past the staged window
+  const int4* __restrict__ qv = s.q;
+  const int* __restrict__ members = s.members;
+  // stage the window: the 64 (start, offset) pairs first, then every thread copies
+  // window entries tid, tid + 256, ... (independent loads, several in flight)
+  __shared__ int2 wtab[WIN_CELLS];
+  const int cap = s.window_cap;
+  int* const wx = wsm;
+  int* const wy = wsm + cap;
+  int* const wz = wsm + 2 * cap;
+  if (threadIdx.x < WIN_CELLS) wtab[threadIdx.x] = s.blk_win[(size_t)b * WIN_CELLS + threadIdx.x];
+  __syncthreads();
+  {
+    constexpr int UNR = 4;
+    for (int e0 = threadIdx.x; e0 < info.z; e0 += UNR * STAGED_BLOCK) {
+      int src[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int e = e0 + u * STAGED_BLOCK;
+        int c = 0;   // last window cell whose offset is <= e
+#pragma unroll
+        for (int step = 32; step > 0; step >>= 1)
+          if (c + step < WIN_CELLS && wtab[c + step].y <= e) c += step;
+        src[u] = e < info.z ? members[wtab[c].x + (e - wtab[c].y)] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+        if (src[u] >= 0) {
+          const int4 q = __ldg(qv + src[u]);
+          const int e = e0 + u * STAGED_BLOCK;
+          wx[e] = q.x;
+          wy[e] = q.y;
+          wz[e] = (q.z & ~3) | q.w;   // type in the two low bits (grid L/2^30 in z)
+        }
+    }
+  }
+  const int nt = s.ntypes;
+  __shared__ PairF tabf[MT == 2 ? MAXT2 : 1];
+  if (MT == 2)
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) tabf[k] = s.pf[k];
+  __syncthreads();
+  const float2 sc0 = make_float2(s.fscale[0], s.fscale[0]);
+  const float2 sc1 = make_float2(s.fscale[1], s.fscale[1]);
+  const float2 sc2 = make_float2(s.fscale[2], s.fscale[2]);
+  const PairF p0 = s.pf[0];
+  const size_t stride = (size_t)s.nl_stride;
+  const int4* __restrict__ nl8 = reinterpret_cast<const int4*>(s.nl);
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int pidx = threadIdx.x; pidx < info.y; pidx += STAGED_BLOCK) {
+    const int m = info.x + pidx;
+    const int i = members[m];
+    int4 qi = qv[i];
+    qi.z &= ~3;   // same z grid as the staged neighbours
+    const int n = s.nn[i];
+    const PairF r0 = MT == 1 ? s.pf[qi.w * nt] : p0;
+    const PairF r1 = MT == 1 ? s.pf[qi.w * nt + nt - 1] : p0;
+    auto par = [&](int tj) -> PairF {
+      if (MT == 0) return p0;
+      if (MT == 1) return tj ? r1 : r0;
+      return tabf[qi.w * nt + tj];
+    };
+    // an empty slot (k >= n) reads window entry 0 and is masked out of the sums
+    auto nb = [&](unsigned word, int k, int half) -> int4 {
+      const unsigned l = k < n ? (half ? word >> 16 : word & 0xffffu) : 0u;
+      const int z = wz[l];
+      return make_int4(wx[l], wy[l], z & ~3, z & 3);
+    };
+    float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx, e = fx;
+    float2 w[6] = {fx, fx, fx, fx, fx, fx};
+    const int groups = (n + 7) >> 3;
+    int4 nxt = groups > 0 ? __ldg(nl8 + m) : make_int4(0, 0, 0, 0);
+    for (int g = 0; g < groups; ++g) {
+      const int4 cur = nxt;
+      if (g + 1 < groups) nxt = __ldg(nl8 + (size_t)(g + 1) * stride + m);
+      const int k0 = g << 3;
+      const unsigned u[4] = {(unsigned)cur.x, (unsigned)cur.y, (unsigned)cur.z, (unsigned)cur.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ka = k0 + 2 * c, kb = ka + 1;
+        const int4 qa = nb(u[c], ka, 0), qb = nb(u[c], kb, 1);
+        pair2<EV>(qi, qa, qb, ka < n, kb < n, sc0, sc1, sc2, par(qa.w), par(qb.w), fx, fy, fz,
+                  e, w);
+      }
+    }
+    s.f32[i] = make_float4(fx.x + fx.y, fy.x + fy.y, fz.x + fz.y, EV ? e.x + e.y : 0.f);
+    if (EV) {
+      double v[7] = {(double)(e.x + e.y)};
+      for (int c = 0; c < 6; ++c) v[c + 1] = (double)(w[c].x + w[c].y);
+      if (s.pp_u) {
+        s.pp_u[i] = v[0];
+        for (int c = 0; c < 6; ++c) s.pp_w[6 * (size_t)i + c] = v[c + 1];
+      }
+      for (int c = 0; c < 7; ++c) acc[c] += v[c];
+    }
+  }
+  if (EV) {   // fixed-order block reduction into this tile's partial sums
+    __shared__ double red[7][STAGED_BLOCK];
+    for (int c = 0; c < 7; ++c) red[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    if (threadIdx.x < 7) {
+      double a = 0;
+      for (int k = 0; k < (int)blockDim.x; ++k) a += red[threadIdx.x][k];
+      s.partials[8 * (size_t)(part_base + blockIdx.x) + threadIdx.x] = a;
+    }
   }
 }
 
+bool tpp_supported(int tpp) { return tpp == 1 || tpp == 2 || tpp == 4; }
+
+template <int PREC, int TPP>
+static void* pick3(int mt, int ev) {
+  if constexpr (PREC == GBMD_FP64) {
+    mt = mt ? 2 : 0;   // one FP64 table mode
+  } else {
+    if (mt == 1) return ev ? (void*)k_force<PREC, TPP, 1, true> : (void*)k_force<PREC, TPP, 1, false>;
+  }
+  if (mt == 2) return ev ? (void*)k_force<PREC, TPP, 2, true> : (void*)k_force<PREC, TPP, 2, false>;
+  return ev ? (void*)k_force<PREC, TPP, 0, true> : (void*)k_force<PREC, TPP, 0, false>;
+}
+
+template <int PREC>
+static void* pick2(int tpp, int mt, int ev) {
+  switch (tpp) {
+    case 1: return pick3<PREC, 1>(mt, ev);
+    case 2: return pick3<PREC, 2>(mt, ev);
+    default: return pick3<PREC, 4>(mt, ev);
+  }
+}
+
+// multi: 0 = one type, 1 = at most two types, 2 = up to MAXT types
 KernelCall force_call(int prec, int multi, int ev, int tpp, int block, const SysDev* d,
                       const Tile* tiles_f, int ntiles, GroupCtl* ctl, int force_all) {
+  // the FP64 kernel is FP64-pipe bound: its table stays in shared memory
   void* f = prec == GBMD_FP64 ? pick2<GBMD_FP64>(tpp, multi, ev) : pick2<GBMD_MIXED>(tpp, multi, ev);
   KernelCall k = make_call(f, ntiles, block, 0);
   put(k, d); put(k, tiles_f); put(k, ctl); put(k, force_all);
+  return k;
+}
+
+KernelCall force_staged_call(int multi, int ev, const SysDev* d, const Tile* tiles_s, int ntiles,
+                             GroupCtl* ctl, int force_all, int part_base, int window_cap) {
+  void* const fs[3][2] = {{(void*)k_force_staged<0, false>, (void*)k_force_staged<0, true>},
+                          {(void*)k_force_staged<1, false>, (void*)k_force_staged<1, true>},
+                          {(void*)k_force_staged<2, false>, (void*)k_force_staged<2, true>}};
+  const int mt = multi < 0 ? 0 : multi > 2 ? 2 : multi;
+  void* f = fs[mt][ev ? 1 : 0];
+  const size_t smem = (size_t)window_cap * 3 * sizeof(int);
+  static bool attr_set[3][2] = {};
+  if (!attr_set[mt][ev ? 1 : 0]) {   // dynamic shared memory above the 48 KB default
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr_set[mt][ev ? 1 : 0] = true;
+  }
+  KernelCall k = make_call(f, ntiles, STAGED_BLOCK, smem);
+  put(k, d); put(k, tiles_s); put(k, ctl); put(k, force_all); put(k, part_base);
   return k;
 }
 

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SysDev* __restrict_
   if (threadIdx.x == 0) {
     carry = 0;
     s.flags->nb_total = 0;
+    s.flags->max_window = 0;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -136,13 +137,17 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* 
     const int v = lane < n ? s.members_tmp[b + lane] : 0x7fffffff;
     int rk = 0;
     for (int k = 0; k < 32; ++k) rk += __shfl_sync(0xffffffffu, v, k) < v;
-    if (lane < n) s.members[b + rk] = v;
+    if (lane < n) {
+      s.members[b + rk] = v;
+      s.rmember[v] = b + rk;
+    }
   } else {
     for (int m = lane; m < n; m += 32) {
       const int v = s.members_tmp[b + m];
       int rk = 0;
       for (int k = 0; k < n; ++k) rk += s.members_tmp[b + k] < v;
       s.members[b + rk] = v;
+      s.rmember[v] = b + rk;
     }
   }
 }
@@ -190,7 +195,67 @@ __global__ void __launch_bounds__(TILE_P) k_copyback(const SysDev* __restrict__ 
   s.rtag[tg] = k;
   s.q[k] = s.q_alt[k];
   s.members[k] = k;
+  s.rmember[k] = k;
   if (s.precision == GBMD_FP64) s.p64[k] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
+}
+
+// ---- staged force tiles: the window of every aligned 2x2x2 block of cells ----
+// One warp per block.  The window is the 4x4x4 cells around the block (the union
+// of its cells' 27-cell stencils; distinct because every axis has >= 4 cells),
+// listed with x fastest; each window cell contributes its member range, placed at
+// a running offset.  The block's own cells have 8 consecutive Morton codes, so
+// their members form one contiguous range.
+__global__ void __launch_bounds__(256) k_blocks(const SysDev* __restrict__ sysv,
+                                                const Tile* __restrict__ tiles, GroupCtl* ctl) {
+  const Tile t = tiles[blockIdx.x];
+  const SysDev& s = sysv[t.sys];
+  count(s, t, ctl);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!rebuilding(s) || !s.staged || w >= t.count) return;
+  const int b = t.first + w;
+  const int nb0 = s.nb[0], nb1 = s.nb[1];
+  const int bx = b % nb0, by = (b / nb0) % nb1, bz = b / (nb0 * nb1);
+  const int nc0 = s.nc[0], nc1 = s.nc[1], nc2 = s.nc[2];
+  int st[2], cn[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int wi = lane + 32 * h;
+    const int cx = (2 * bx - 1 + (wi & 3) + nc0) % nc0;
+    const int cy = (2 * by - 1 + ((wi >> 2) & 3) + nc1) % nc1;
+    const int cz = (2 * bz - 1 + (wi >> 4) + nc2) % nc2;
+    const int r = s.lin2rank[(cz * nc1 + cy) * nc0 + cx];
+    st[h] = s.cell_start[r];
+    cn[h] = s.cell_start[r + 1] - st[h];
+  }
+  int p0 = cn[0], p1 = cn[1];   // inclusive prefixes
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y0 = __shfl_up_sync(0xffffffffu, p0, o);
+    const int y1 = __shfl_up_sync(0xffffffffu, p1, o);
+    if (lane >= o) {
+      p0 += y0;
+      p1 += y1;
+    }
+  }
+  const int tot0 = __shfl_sync(0xffffffffu, p0, 31);
+  const int wtot = tot0 + __shfl_sync(0xffffffffu, p1, 31);
+  s.blk_win[(size_t)b * WIN_CELLS + lane] = make_int2(st[0], p0 - cn[0]);
+  s.blk_win[(size_t)b * WIN_CELLS + 32 + lane] = make_int2(st[1], tot0 + p1 - cn[1]);
+  // the block's own cells: lanes 0..7 take (ox, oy, oz)
+  int rk = 0x7fffffff;
+  bool exists = false;
+  if (lane < 8) {
+    const int cx = 2 * bx + (lane & 1), cy = 2 * by + ((lane >> 1) & 1), cz = 2 * bz + (lane >> 2);
+    exists = cx < nc0 && cy < nc1 && cz < nc2;
+    if (exists) rk = s.lin2rank[(cz * nc1 + cy) * nc0 + cx];
+  }
+  const int nown = __popc(__ballot_sync(0xffffffffu, exists));
+  for (int o = 16; o > 0; o >>= 1) rk = min(rk, __shfl_xor_sync(0xffffffffu, rk, o));
+  if (lane == 0) {
+    const int first = s.cell_start[rk];
+    s.blk_info[b] = make_int4(first, s.cell_start[rk + nown] - first, wtot, 0);
+    atomicMax(&s.flags->max_window, wtot);
+    if (wtot > s.window_cap) atomicCAS(&s.flags->error, 0, (int)DEV_WINDOW);
+  }
 }
 
 // ---- FP64 decision for a candidate in the band: the reference definition ----
@@ -251,6 +316,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   __shared__ float thr_lo[CELLS_PER_TILE][MAXT2], thr_hi[CELLS_PER_TILE][MAXT2];
   __shared__ double rl2d[CELLS_PER_TILE][MAXT2];
   __shared__ float4 cand[CELLS_PER_TILE][32];
+  __shared__ int cand_l[CELLS_PER_TILE][32];   // staged: window-local index of the candidate
   for (int k = lane; k < nt * nt; k += 32) {
     const float rl2 = s.pf[k].rl2;
     thr_lo[w][k] = rl2 * (1.0f - NL_BAND);
@@ -269,13 +335,19 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   const int lo1 = nc1 >= 3 ? -1 : 0, n1 = nc1 >= 3 ? 3 : nc1;
   const int lo2 = nc2 >= 3 ? -1 : 0, n2 = nc2 >= 3 ? 3 : nc2;
   const int nsc = n0 * n1 * n2;   // <= 27
-  int sc_start = 0, sc_cnt = 0;
+  int sc_start = 0, sc_cnt = 0, sc_woff = 0;
+  const bool staged = s.staged != 0;   // then every axis has >= 4 cells (lo = -1)
+  const int blk = ((cz >> 1) * s.nb[1] + (cy >> 1)) * s.nb[0] + (cx >> 1);
   if (lane < nsc) {
     const int dx = lo0 + lane % n0, dy = lo1 + (lane / n0) % n1, dz = lo2 + lane / (n0 * n1);
     const int x = (cx + dx + nc0) % nc0, y = (cy + dy + nc1) % nc1, z = (cz + dz + nc2) % nc2;
     const int nr = s.lin2rank[(z * nc1 + y) * nc0 + x];
     sc_start = s.cell_start[nr];
     sc_cnt = s.cell_start[nr + 1] - sc_start;
+    if (staged) {   // this stencil cell's place in the block's 4x4x4 window
+      const int wi = (((cz & 1) + 1 + dz) * 4 + ((cy & 1) + 1 + dy)) * 4 + ((cx & 1) + 1 + dx);
+      sc_woff = s.blk_win[(size_t)blk * WIN_CELLS + wi].y;
+    }
   }
   int incl = sc_cnt;   // inclusive prefix of the stencil cells' sizes
   for (int o = 1; o < 32; o <<= 1) {
@@ -292,7 +364,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
 
   // candidate c of the flattened stream, relative to the cell centre; every lane
   // runs every shuffle
-  auto fetch = [&](int c) -> float4 {
+  auto fetch = [&](int c, int& local) -> float4 {
     int lo = 0;
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1) {
@@ -302,6 +374,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     }
     const int st = __shfl_sync(0xffffffffu, sc_start, lo);
     const int ex = __shfl_sync(0xffffffffu, excl, lo);
+    local = __shfl_sync(0xffffffffu, sc_woff, lo) + (c - ex);
     if (c >= total) return make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
     const int j = members[st + (c - ex)];
     const int4 qj = qv[j];
@@ -334,11 +407,15 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     const int stride = s.nl_stride;
     const int i_row = valid ? i : 0;
     int cnt = 0;
-    float4 next = fetch(lane);
+    const int m_row = ibase + lane;   // member rank (staged list rows)
+    unsigned short* __restrict__ nl16 = reinterpret_cast<unsigned short*>(s.nl);
+    int next_l = 0;
+    float4 next = fetch(lane, next_l);
     for (int cb = 0; cb < total; cb += 32) {
       cand[w][lane] = next;
+      cand_l[w][lane] = next_l;
       __syncwarp();
-      if (cb + 32 < total) next = fetch(cb + 32 + lane);   // in flight during the tests
+      if (cb + 32 < total) next = fetch(cb + 32 + lane, next_l);   // in flight during the tests
       const int m = min(32, total - cb);
       unsigned mask = 0;
       auto test = [&](int k) {
@@ -388,8 +465,9 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
         }
         const int p = MULTI ? pt + ((unsigned)cw >> NL_TYPE_SHIFT) : 0;
         const bool keep = r2 < thr_lo[w][p] || exact_within(s, i, j, rl2d[w][p]);
-        if (keep) {
-          nl[nl_index(i_row, min(cnt, cap - 1), stride)] = j;   // an overflowing row is rebuilt
+        if (keep) {   // an overflowing row is rebuilt anyway
+          if (staged) nl16[nl16_index(m_row, min(cnt, cap - 1), stride)] = (unsigned short)cand_l[w][k];
+          else nl[nl_index(i_row, min(cnt, cap - 1), stride)] = j;
           ++cnt;
         }
       }
@@ -422,6 +500,7 @@ SIMPLE_CALL(scatter_call, k_scatter, TILE_P)
 SIMPLE_CALL(cellsort_call, k_cellsort, CELLS_PER_TILE * 32)
 SIMPLE_CALL(permute_call, k_permute, TILE_P)
 SIMPLE_CALL(copyback_call, k_copyback, TILE_P)
+SIMPLE_CALL(blocks_call, k_blocks, 256)
 #undef SIMPLE_CALL
 
 KernelCall nlist_call(const SysDev* d, const Tile* tl, int ntiles, GroupCtl* ctl, bool rel,

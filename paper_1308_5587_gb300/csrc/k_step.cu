@@ -302,8 +302,30 @@ __global__ void __launch_bounds__(TILE_P) k_nlist_export(const SysDev* __restric
     return;
   }
   int* out = idx + (size_t)tg * cap_out;
+  // staged lists hold window-local indices: map them back through the block's window
+  const int2* bw = nullptr;
+  const unsigned short* nl16 = reinterpret_cast<const unsigned short*>(s.nl);
+  int m = 0;
+  if (s.staged) {
+    const int4 qb = s.q_build[i];
+    const int cx = cell_of_fixed(qb.x, s.nc[0]), cy = cell_of_fixed(qb.y, s.nc[1]),
+              cz = cell_of_fixed(qb.z, s.nc[2]);
+    const int b = ((cz >> 1) * s.nb[1] + (cy >> 1)) * s.nb[0] + (cx >> 1);
+    bw = s.blk_win + (size_t)b * WIN_CELLS;
+    m = s.rmember[i];
+  }
   for (int k = 0; k < nn; ++k) {   // insertion sort of the tags (rows are short)
-    int v = s.tag[s.nl[nl_index(i, k, s.nl_stride)]];
+    int j;
+    if (s.staged) {
+      const int local = nl16[nl16_index(m, k, s.nl_stride)];
+      int c = 0;   // last window cell whose offset is <= local
+      for (int step = 32; step > 0; step >>= 1)
+        if (c + step < WIN_CELLS && bw[c + step].y <= local) c += step;
+      j = s.members[bw[c].x + (local - bw[c].y)];
+    } else {
+      j = s.nl[nl_index(i, k, s.nl_stride)];
+    }
+    const int v = s.tag[j];
     int p = k;
     while (p > 0 && out[p - 1] > v) {
       out[p] = out[p - 1];

@@ -7,6 +7,7 @@
 namespace gbmd {
 
 constexpr int TILE_P = 256;     // particles per block of the streaming kernels
+constexpr int EV_TILE_P = 128;  // particles per FP64 energy/virial partial sum
 constexpr int CELLS_PER_TILE = 8;   // warps (= cells) per block of the cell kernels
 constexpr int SCAN_THREADS = 1024;
 
@@ -37,6 +38,8 @@ KernelCall scatter_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupC
 KernelCall cellsort_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl* ctl);
 KernelCall permute_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
 KernelCall copyback_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
+// window table of every staged 2x2x2 block (8 blocks per kernel block of 256)
+KernelCall blocks_call(const SysDev* d, const Tile* tiles_b, int ntiles, GroupCtl* ctl);
 KernelCall nlist_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl* ctl, bool rel,
                       bool multi);
 // pair force (K5): ev = 0 forces only, 1 also energy/virial partial sums
@@ -44,6 +47,11 @@ KernelCall nlist_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl
 // per-step activity flag (used outside the step graph)
 KernelCall force_call(int prec, int multi, int ev, int tpp, int block, const SysDev* d,
                       const Tile* tiles_f, int ntiles, GroupCtl* ctl, int force_all);
+// staged pair force: one kernel block per 2x2x2 cell block, window in shared memory
+// (mixed precision); part_base = first partial-sum slot of these tiles
+KernelCall force_staged_call(int multi, int ev, const SysDev* d, const Tile* tiles_s, int ntiles,
+                             GroupCtl* ctl, int force_all, int part_base, int window_cap);
+constexpr int STAGED_BLOCK = 256;
 // thermo reduction (K7), one block per system
 KernelCall thermo_call(const SysDev* d, const Tile* tiles_s, int nsys, GroupCtl* ctl);
 // import row-major tag-order staging -> internal arrays; export the reverse

@@ -40,7 +40,11 @@ class gbmd_desc(C.Structure):
                 ("rcut", C.c_void_p), ("r_buff", C.c_double), ("dt", C.c_double),
                 ("mass", C.c_double), ("precision", C.c_int32), ("sort_period", C.c_int32),
                 ("nlist_capacity", C.c_int32), ("threads_per_particle", C.c_int32),
-                ("stream", C.c_void_p), ("device", C.c_int32)]
+                ("stream", C.c_void_p), ("device", C.c_int32), ("force_path", C.c_int32)]
+
+
+GBMD_PATH_GLOBAL, GBMD_PATH_STAGED = 0, 1
+FORCE_PATHS = {"global": GBMD_PATH_GLOBAL, "staged": GBMD_PATH_STAGED}
 
 
 class gbmd_thermo(C.Structure):
@@ -60,7 +64,8 @@ class gbmd_info(C.Structure):
                 ("threads_per_particle", C.c_int32), ("force_block", C.c_int32),
                 ("step", C.c_int64), ("n_rebuilds", C.c_int64), ("n_sorts", C.c_int64),
                 ("kernel_launches", C.c_int64), ("neighbors_total", C.c_int64),
-                ("footprint_bytes", C.c_int64)]
+                ("footprint_bytes", C.c_int64), ("force_path", C.c_int32),
+                ("max_window", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -147,7 +152,7 @@ def _stream_handle(stream):
 
 def make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass, precision,
               sort_period=0, nlist_capacity=0, threads_per_particle=0, stream=None,
-              image=None, device=False, cuda_device=-1):
+              image=None, device=False, cuda_device=-1, force_path="global"):
     """Build a gbmd_desc; returns (desc, keepalive) -- keep the second alive."""
     eps = np.atleast_2d(np.asarray(eps, np.float64))
     nt = eps.shape[0]
@@ -180,6 +185,7 @@ def make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass, preci
     d.threads_per_particle = int(threads_per_particle)
     d.stream = _stream_handle(stream)
     d.device = int(cuda_device)
+    d.force_path = FORCE_PATHS.get(force_path, force_path) if isinstance(force_path, str) else int(force_path)
     return d, keep
 
 
@@ -351,11 +357,11 @@ class System:
     def __init__(self, pos, vel, box, types=None, eps=1.0, sigma=1.0, rcut=2.5, r_buff=0.4,
                  dt=0.005, mass=1.0, precision="mixed", sort_period=0, nlist_capacity=0,
                  threads_per_particle=0, stream=None, image=None, device=False, n=None,
-                 cuda_device=-1):
+                 cuda_device=-1, force_path="global"):
         n = int(n if n is not None else np.asarray(pos).reshape(-1, 3).shape[0])
         desc, keep = make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass,
                                precision, sort_period, nlist_capacity, threads_per_particle,
-                               stream, image, device, cuda_device)
+                               stream, image, device, cuda_device, force_path)
         self.n = n
         self.box = np.broadcast_to(np.asarray(box, np.float64), (3,)).copy()
         self.precision = precision

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.gbmd_abi_version() == 1
+    assert lib.gbmd_abi_version() == 2
 
 
 def _desc(lib, **over):
@@ -64,6 +64,7 @@ def _desc(lib, **over):
     (dict(types=np.array([0, 1, 0, 0], np.int32)), "BAD_ARG"),      # type >= ntypes
     (dict(pos=np.full((4, 3), np.nan)), "BAD_ARG"),
     (dict(threads_per_particle=3), "BAD_ARG"),
+    (dict(force_path=2), "BAD_ARG"),
     (dict(eps=np.array([[1.0, 2.0], [1.5, 1.0]])), "BAD_ARG"),     # not symmetric
 ])
 def test_create_rejects_bad_arguments_on_the_host(lib, bad, status):

@@ -343,3 +343,61 @@ def test_sampled_forces_full_size_ka_1m():
     assert info["n_sorts"] >= 2 and info["step"] == 200
     assert np.linalg.norm(F.sum(0)) <= 1e-5 * np.abs(F).sum()
     s.close()
+
+
+def _system_with_path(w, staged, **kw):
+    return gbmd.System.from_workload(w, precision="mixed",
+                                     force_path="staged" if staged else "global", **kw)
+
+
+@pytest.mark.parametrize("binary", [False, True])
+def test_staged_and_global_force_paths_agree(binary):
+    """The shared-memory (staged) force path and the global-index path give the same
+    forces (to FP32 summation order) and the same neighbour sets."""
+    w = (wl.lj_fluid(6000, 1.2, 1.0, seed=201, binary=True, r_buff=0.3) if binary
+         else wl.lj_fluid(6000, 0.84, 1.2, seed=202))
+    a = _system_with_path(w, True)
+    b = _system_with_path(w, False)
+    assert a.info()["force_path"] == 1 and b.info()["force_path"] == 0
+    for s in (a, b):
+        s.step(60)
+    Fa, Fb = a.forces(), b.forces()
+    pa, pb = a.state()[0], b.state()[0]
+    assert np.abs(mi(pa - pb, w.box)).max() < 1e-4
+    Fo, _, _, _, _ = oracle.forces(pa, w.box, w.types, w.pairs.as_dict())
+    assert rel_l2(Fa, Fo) <= 1e-5
+    st = a.state()
+    a.set_state(*st)          # rebuild the lists at the positions compared below
+    ca, ia = a.neighbors(cap=512)
+    pos = a.state()[0]
+    rl = w.pairs.rcut + w.r_buff
+    pairs, r = oracle.neighbors(pos, w.box, w.types, rl)
+    ok = np.abs(r - rl[w.types[pairs[:, 0]], w.types[pairs[:, 1]]]) > 1e-9
+    ref = {(int(x), int(y)) for x, y in pairs[ok]}
+    band = {(int(x), int(y)) for x, y in pairs[~ok]}
+    mine = set()
+    for i in range(w.n):
+        for j in ia[i, :ca[i]]:
+            mine.add((min(i, int(j)), max(i, int(j))))
+    assert mine - band == ref
+    ta, tb = a.thermo(), b.thermo()
+    assert ta["pe"] == pytest.approx(tb["pe"], rel=1e-5)
+    a.close()
+    b.close()
+
+
+def test_staged_window_overflow_falls_back():
+    """A dense cluster in a large box: the staged windows exceed shared memory at the
+    first build, the system falls back to global indices, and forces stay right."""
+    blob = wl.lj_fluid(4000, 1.2, 1.0, seed=203)
+    box = np.full(3, 60.0)
+    s = _system_with_path(
+        wl.Workload(blob.pos, blob.vel, blob.types, box, blob.pairs, r_buff=1.5), True)
+    info = s.info()
+    assert info["force_path"] == 0
+    F = s.forces()
+    Fo, *_ = oracle.forces(s.state()[0], box, None, blob.pairs.as_dict())
+    assert rel_l2(F, Fo) <= 1e-5
+    s.step(20)
+    assert s.state()[3] == 20
+    s.close()

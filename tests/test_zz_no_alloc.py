@@ -61,13 +61,29 @@ def test_noalloc_thermo_matches_allocating_thermo(prec):
 
 
 def test_noalloc_thermo_rejects_systems_over_the_limit():
-    w = wl.lj_fluid(270000, 0.84, 1.2, seed=503)
-    s = gbmd.System.from_workload(w, precision="mixed")
-    s.set_tuning(4, 32)        # eight particles per force tile -> 33,750 tiles > 32,768
+    # global force path: 128 particles per energy tile, so 4,194,304 particles at most
+    w = wl.lj_fluid(4_200_000, 0.84, 1.2, seed=503)
+    s = gbmd.System.from_workload(w, precision="mixed", force_path="global")
     with pytest.raises(gbmd.GbmdError) as e:
         gbmd.gbmd_get_thermo_noalloc(s.handle)
     assert e.value.status == "BAD_ARG"
     assert "allocation-free limit" in str(e.value)
-    s.set_tuning(2, 256)
-    _same(gbmd.gbmd_get_thermo_noalloc(s.handle), gbmd.gbmd_get_thermo(s.handle), "mixed")
+    t = gbmd.gbmd_get_thermo(s.handle)          # the allocating readout still works
+    assert math.isfinite(t["pe"]) and t["pe"] < 0
+    s.close()
+
+
+def test_noalloc_thermo_does_not_depend_on_the_force_tuning():
+    # the energy launch has its own fixed tiles: the FP64 sums are bitwise the same
+    # for every block size at one threads-per-particle setting
+    w = wl.lj_fluid(5000, 0.84, 1.2, seed=504)
+    s = gbmd.System.from_workload(w, precision="fp64")
+    s.step(10)
+    ref = gbmd.gbmd_get_thermo_noalloc(s.handle)
+    for block in (64, 128, 256, 512):
+        s.set_tuning(2, block)
+        t = gbmd.gbmd_get_thermo_noalloc(s.handle)
+        assert t["pe"] == ref["pe"] and t["virial"] == ref["virial"]
+        t2 = gbmd.gbmd_get_thermo(s.handle)
+        assert t2["pe"] == ref["pe"]
     s.close()
