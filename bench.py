@@ -283,6 +283,25 @@ def cpu_baseline(w, world_rank):
                       "scaled per particle-step"}
 
 
+def cpu_single_thread(w):
+    """The same oracle on one core: forces of a sample of particles against all N."""
+    import oracle
+    oracle.build()
+    p = w.pairs.as_dict()
+    m = min(w.n, 256)
+    idx = np.random.default_rng(0).choice(w.n, m, replace=False)
+    old = oracle.get_threads()
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.forces_subset(w.pos, w.box, w.types, p, idx)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(old)
+    return {"value": m / dt, "unit": UNIT, "cores": 1,
+            "sample": f"forces on {m} sampled particles against all {w.n} ({dt:.2f} s)"}
+
+
 def gpu_arm(args):
     import torch
     from paper_1308_5587_gb300 import _build, gbmd
@@ -337,6 +356,18 @@ def gpu_arm(args):
                 "force_ms_mean": round(f_mean, 5), "peak_kind": f"of {peak_kind}",
                 "force_share_of_step": round(f_mean / float(step_ms.mean()), 3)}
 
+    # second line: the whole step.  Integrate reads F, v, x, type, x_build-shadow and
+    # writes v, x, the shadow (mixed 148 B/particle; FP64 adds 16 B of F and a 32 B
+    # FP64 shadow); each rebuild writes the list (4 <n>) and ~60 B of cell-list and
+    # count traffic per particle.
+    reb = info["n_rebuilds"] / max(info["step"], 1)
+    int_bytes = 148 if precision == "mixed" else 196
+    step_bytes = alg_bytes + n * (int_bytes + reb * (60 + 4 * nbar))
+    step_achieved = step_bytes / (float(step_ms.mean()) * 1e-3) / 1e9
+    roofline_step = {"bound": "hbm", "achieved": round(step_achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(step_achieved / peak, 4),
+                     "alg_bytes_per_step": int(step_bytes), "peak_kind": f"of {peak_kind}"}
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -353,7 +384,8 @@ def gpu_arm(args):
                       "force_block": info["force_block"], "nlist_capacity": info["nlist_capacity"],
                       "force_path": "staged" if info["force_path"] == 1 else "global",
                       "sort_period": sort_period},
-           "tps": args.steps / t_max, "roofline": roofline, "clocks": clk,
+           "tps": args.steps / t_max, "roofline": roofline, "roofline_step": roofline_step,
+           "clocks": clk,
            "gpu_launches": int(launches),
            "rebuilds_per_step": None}
     out["rebuilds_per_step"] = round(info["n_rebuilds"] / max(info["step"], 1), 4)
@@ -385,6 +417,154 @@ def gpu_arm(args):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, rank)
+        out["cpu_baseline"]["single_thread"] = cpu_single_thread(w)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched ensemble: 256 replicas stepped together (one launch per kernel per step)
+# ---------------------------------------------------------------------------
+
+class _BatchStepper:
+    """The batch seen through the calls timed_steps makes on a system."""
+
+    def __init__(self, batch, systems):
+        self.b, self.systems = batch, systems
+
+    def step(self, k):
+        self.b.step(k)
+
+    def sync(self):
+        self.b.sync()
+
+    def info(self):
+        return {"kernel_launches": self.b.info()["kernel_launches"]}
+
+    def set_force_events(self, a, b):
+        self.systems[0].set_force_events(a, b)   # events live in the batch's step graph
+
+
+def batch_arm(args):
+    import torch
+    from paper_1308_5587_gb300 import _build, gbmd, workloads as wl
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world)
+    _build.build()
+    stream = torch.cuda.current_stream()
+    params = wl.replica_params(args.replicas, seed=wl.BASE_SEED + 1000 * rank)
+    ws = [wl.replica(*p) for p in params]
+    b = gbmd.Batch("mixed", stream=stream.cuda_stream, cuda_device=local)
+    systems = [gbmd.System.from_workload(w, precision="mixed", sort_period=100,
+                                         stream=stream.cuda_stream, cuda_device=local)
+               for w in ws]
+    for x in systems:
+        b.add(x)
+    if not args.no_autotune:
+        b.autotune(None)
+    n = sum(w.n for w in ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, force_ms, launches = timed_steps(torch, _BatchStepper(b, systems), args.steps,
+                                              args.warmup, None, stream, dist)
+    clk = clocks.stop()
+    infos = [x.info() for x in systems]
+    tune = (infos[0]["threads_per_particle"], infos[0]["force_block"])
+    th = [x.thermo() for x in systems[:4]]
+    assert all(math.isfinite(t["pe"]) for t in th)
+    t_max = reduce_scalar(dist, float(step_ms.sum()) / 1e3, "max")
+    value = reduce_scalar(dist, n * args.steps, "sum") / t_max
+    alg_bytes = sum(i["n"] * (16 + 4 + 16) + 4 * i["neighbors_total"] for i in infos)
+    peak, peak_kind = measured_peaks()
+    f_mean = float(force_ms.mean())
+    achieved = alg_bytes / (f_mean * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 pair forces + f64 integration",
+           "data": "synthetic (seeded FCC + jitter, Maxwell-Boltzmann; no dataset)",
+           "config": {"workload": f"batched ensemble: {len(ws)} LJ replicas, N_k log-uniform "
+                                  "[500, 20000], rho U(0.7, 0.9), T U(0.8, 1.5), rc 2.5, "
+                                  "rbuff 0.4, dt 0.005, mixed",
+                      "n": n, "replicas": len(ws), "precision": "mixed",
+                      "parallelism": f"replicas x{world}" if world > 1 else "one batch",
+                      "l2": "inputs larger than L2", "timed_iteration":
+                          "one step of every replica (one single-step CUDA graph)",
+                      "threads_per_particle": tune[0], "force_block": tune[1]},
+           "tps": args.steps / t_max,
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                        "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                        "kernel": "k_force<mixed> over all replicas",
+                        "alg_bytes_per_launch": int(alg_bytes), "force_ms_mean": round(f_mean, 5),
+                        "peak_kind": f"of {peak_kind}"},
+           "clocks": clk, "gpu_launches": int(launches),
+           "e2e": None}
+    for slot in list(b.members):
+        b.remove(slot).close()
+    b.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# served stream: Poisson arrivals, continuous batching under an HBM budget
+# ---------------------------------------------------------------------------
+
+def serve_arm(args):
+    import torch
+    from paper_1308_5587_gb300 import _build, serve, workloads as wl
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world)
+    _build.build()
+    stream = torch.cuda.current_stream()
+    be = serve.GpuBackend("mixed", stream=stream.cuda_stream, cuda_device=local)
+    # warm-up request (module load, first graph capture): not part of the trace
+    serve.Scheduler(be, 1 << 40).run([serve.Request(-1, 0.0, 50, 4000,
+                                                    dict(n=4000, rho=0.8, T=1.0, seed=1))])
+    trace = wl.request_trace(args.requests, args.rate, seed=wl.BASE_SEED + 1000 * rank)
+    reqs = serve.requests_from_trace(trace)
+    budget = int(args.budget_gb * 1e9)
+    sch = serve.Scheduler(be, budget, max_quantum=args.quantum)
+    launches0 = be.batch.info()["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    summ = sch.run(reqs)
+    clk = clocks.stop()
+    launches = be.batch.info()["kernel_launches"] - launches0
+    be.close()
+    done = [r for r in summ.records if r.finished is not None]
+    t_max = reduce_scalar(dist, summ.makespan, "max")
+    value = reduce_scalar(dist, summ.particle_steps, "sum") / t_max
+    steps = sum(r.steps for r in done)
+    up = sum(r.n * (24 + 24 + 4) for r in done)     # positions, velocities, types
+    down = sum(8 * 11 for r in done)                # thermodynamic record per request
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": steps, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair forces + f64 integration",
+           "data": "synthetic (seeded Poisson request trace; seeded LJ fluids)",
+           "config": {"workload": f"served stream: {len(reqs)} requests, Poisson "
+                                  f"{args.rate}/s, N log-uniform [256, 200000], rho U(0.7, 0.9), "
+                                  "T U(0.8, 1.5), steps U{1000..50000}, rc 2.5, rbuff 0.4, "
+                                  "dt 0.005, mixed",
+                      "budget_bytes": budget, "max_quantum": args.quantum,
+                      "parallelism": f"replicas x{world}" if world > 1 else "one batch"},
+           "latency_s": {"p50": summ.p50, "p99": summ.p99, "mean": summ.mean,
+                         "completed": len(done),
+                         "rejected": sum(r.rejected for r in summ.records)},
+           "makespan_s": summ.makespan, "quanta": summ.quanta,
+           "peak_resident_bytes": summ.peak_resident_bytes,
+           "clocks": clk, "gpu_launches": int(launches),
+           "e2e": {"value": value, "unit": UNIT,
+                   "h2d_bytes_per_step": int(up / max(steps, 1)),
+                   "d2h_bytes_per_step": int(down / max(steps, 1)),
+                   "loop": "whole trace: host inputs generated and uploaded at admission, "
+                           "results read back at retirement"}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -403,6 +583,9 @@ def reference_arm(args):
     oracle.build()
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
+    if args.workload in ("batch", "serve"):
+        raise SystemExit("--impl reference times the single-system workloads "
+                         "(lj64k, ka1m, plain4k)")
     w, precision, sort_period, wdesc = make_workload(args.workload, 0)
     p = w.pairs.as_dict()
     n = w.n
@@ -453,7 +636,14 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["gbmd", "reference"], default="gbmd")
-    ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k"], default="lj64k")
+    ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k", "batch", "serve"],
+                    default="lj64k")
+    ap.add_argument("--replicas", type=int, default=256, help="batch workload: replicas")
+    ap.add_argument("--no-autotune", action="store_true", help="batch workload: fixed tuning")
+    ap.add_argument("--requests", type=int, default=200, help="serve workload: trace length")
+    ap.add_argument("--rate", type=float, default=50.0, help="serve workload: arrivals per s")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serve workload: HBM budget")
+    ap.add_argument("--quantum", type=int, default=2000, help="serve workload: max steps per quantum")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--force-path", choices=["global", "staged"], default="global",
                     help="neighbour gather through L1/L2 by 32-bit index (default) or "
@@ -470,6 +660,10 @@ def main(argv=None):
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "batch":
+        batch_arm(args)
+    elif args.workload == "serve":
+        serve_arm(args)
     else:
         gpu_arm(args)
 

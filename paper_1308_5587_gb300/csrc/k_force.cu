@@ -6,7 +6,8 @@
 // neighbour j of particle i with r^2 < r_cut,ij^2 (strict):
 //   F_i += f d_ij,  f = 24 eps [2 (sigma/r)^12 - (sigma/r)^6] / r^2,  d_ij = x_i - x_j,
 // and optionally u_i += 1/2 (4 eps [(sigma/r)^12 - (sigma/r)^6] - V_LJ(r_cut)) and
-// W_i,ab += 1/2 d_a f d_b, whose per-tile sums are reduced in FP64.
+// W_i,ab += 1/2 d_a f d_b, whose per-tile sums are reduced in FP64 together with the
+// sum of v_i . v_i (kinetic energy, from the full-step velocity).
 //
 // List layout (ELL4): entry k of particle i is nl[((k / 4) * stride + i) * 4 + k % 4]
 // with stride = N rounded up to 32, so one int4 holds 4 consecutive entries of one
@@ -51,21 +52,37 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
-// FP64 block reduction of 7 per-particle values into partials[tile][0..6] (fixed order)
+// FP64 block reduction of NPART per-particle values into partials[tile][0..7]
+// (fixed order)
+constexpr int NPART = 8;   // energy, virial xx xy xz yy yz zz, sum of v^2
 template <int TPP, int BLOCK_MAX>
 __device__ void reduce_partials(const double* vals, double* out) {
   constexpr int GMAX = BLOCK_MAX / TPP;
-  __shared__ double sh[7][GMAX];
+  __shared__ double sh[NPART][GMAX];
   const int g = threadIdx.x / TPP, l = threadIdx.x % TPP;
   const int ng = blockDim.x / TPP;
   if (l == 0)
-    for (int c = 0; c < 7; ++c) sh[c][g] = vals[c];
+    for (int c = 0; c < NPART; ++c) sh[c][g] = vals[c];
   __syncthreads();
-  if (threadIdx.x < 7) {
+  if (threadIdx.x < NPART) {
     double acc = 0;
     for (int k = 0; k < ng; ++k) acc += sh[threadIdx.x][k];
     out[threadIdx.x] = acc;
   }
+}
+
+// v_i . v_i at full step: the stored velocity is half a kick (h F_i) behind unless
+// v_full; F_i is the force just computed (bitwise the stepping kernel's)
+__device__ __forceinline__ double vsq(const SysDev& s, int i, double fx, double fy, double fz,
+                                      int vfull) {
+  const size_t n = (size_t)s.n;
+  double v0 = s.v[i], v1 = s.v[n + i], v2 = s.v[2 * n + i];
+  if (!vfull) {
+    v0 = fma(s.h, fx, v0);
+    v1 = fma(s.h, fy, v1);
+    v2 = fma(s.h, fz, v2);
+  }
+  return v0 * v0 + v1 * v1 + v2 * v2;
 }
 
 // two neighbours (a, b) of particle i in packed FP32x2 arithmetic; masks ok_a/ok_b
@@ -185,8 +202,9 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
     }
     if (valid && h == 0) s.f32[i] = make_float4(Fx, Fy, Fz, EV ? E : 0.f);
     if (EV) {
-      double vals[7] = {valid ? (double)E : 0.0};
+      double vals[NPART] = {valid ? (double)E : 0.0};
       for (int c = 0; c < 6; ++c) vals[c + 1] = valid ? (double)W[c] : 0.0;
+      vals[7] = valid ? vsq(s, i, Fx, Fy, Fz, ((const volatile Flags*)s.flags)->v_full) : 0.0;
       if (valid && h == 0 && s.pp_u) {
         s.pp_u[i] = vals[0];
         for (int c = 0; c < 6; ++c) s.pp_w[6 * (size_t)i + c] = vals[c + 1];
@@ -254,8 +272,9 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
     }
     if (valid && h == 0) s.f64[i] = make_double4_32a(fx, fy, fz, EV ? e : 0.0);
     if (EV) {
-      double vals[7] = {valid ? e : 0.0,  valid ? w0 : 0.0, valid ? w1 : 0.0, valid ? w2 : 0.0,
-                        valid ? w3 : 0.0, valid ? w4 : 0.0, valid ? w5 : 0.0};
+      double vals[NPART] = {valid ? e : 0.0,  valid ? w0 : 0.0, valid ? w1 : 0.0, valid ? w2 : 0.0,
+                            valid ? w3 : 0.0, valid ? w4 : 0.0, valid ? w5 : 0.0,
+                            valid ? vsq(s, i, fx, fy, fz, ((const volatile Flags*)s.flags)->v_full) : 0.0};
       if (valid && h == 0 && s.pp_u) {
         s.pp_u[i] = vals[0];
         for (int c = 0; c < 6; ++c) s.pp_w[6 * (size_t)i + c] = vals[c + 1];
@@ -336,7 +355,8 @@ __global__ void __launch_bounds__(STAGED_BLOCK) k_force_staged(const SysDev* __r
   const PairF p0 = s.pf[0];
   const size_t stride = (size_t)s.nl_stride;
   const int4* __restrict__ nl8 = reinterpret_cast<const int4*>(s.nl);
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  double acc[NPART] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const int vfull = EV ? ((const volatile Flags*)s.flags)->v_full : 1;
   for (int pidx = threadIdx.x; pidx < info.y; pidx += STAGED_BLOCK) {
     const int m = info.x + pidx;
     const int i = members[m];
@@ -373,22 +393,24 @@ __global__ void __launch_bounds__(STAGED_BLOCK) k_force_staged(const SysDev* __r
                   e, w);
       }
     }
-    s.f32[i] = make_float4(fx.x + fx.y, fy.x + fy.y, fz.x + fz.y, EV ? e.x + e.y : 0.f);
+    const float Fx = fx.x + fx.y, Fy = fy.x + fy.y, Fz = fz.x + fz.y;
+    s.f32[i] = make_float4(Fx, Fy, Fz, EV ? e.x + e.y : 0.f);
     if (EV) {
-      double v[7] = {(double)(e.x + e.y)};
+      double v[NPART] = {(double)(e.x + e.y)};
       for (int c = 0; c < 6; ++c) v[c + 1] = (double)(w[c].x + w[c].y);
+      v[7] = vsq(s, i, Fx, Fy, Fz, vfull);
       if (s.pp_u) {
         s.pp_u[i] = v[0];
         for (int c = 0; c < 6; ++c) s.pp_w[6 * (size_t)i + c] = v[c + 1];
       }
-      for (int c = 0; c < 7; ++c) acc[c] += v[c];
+      for (int c = 0; c < NPART; ++c) acc[c] += v[c];
     }
   }
   if (EV) {   // fixed-order block reduction into this tile's partial sums
-    __shared__ double red[7][STAGED_BLOCK];
-    for (int c = 0; c < 7; ++c) red[c][threadIdx.x] = acc[c];
+    __shared__ double red[NPART][STAGED_BLOCK];
+    for (int c = 0; c < NPART; ++c) red[c][threadIdx.x] = acc[c];
     __syncthreads();
-    if (threadIdx.x < 7) {
+    if (threadIdx.x < NPART) {
       double a = 0;
       for (int k = 0; k < (int)blockDim.x; ++k) a += red[threadIdx.x][k];
       s.partials[8 * (size_t)(part_base + blockIdx.x) + threadIdx.x] = a;

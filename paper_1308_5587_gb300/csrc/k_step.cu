@@ -167,36 +167,20 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// U, sum v.v and W (6) of one system from the per-tile partial sums that the
+// energy variant of the force kernel wrote just before (fixed order: each thread
+// sums tiles t, t + 256, ... in order, then a fixed tree over the threads)
 __global__ void __launch_bounds__(256) k_thermo(const SysDev* __restrict__ sysv,
                                                 const Tile* __restrict__ tiles) {
   __shared__ double sh[256];
   const SysDev& s = sysv[tiles[blockIdx.x].sys];
   if (threadIdx.x == 0) atomicAdd(&s.flags->launches, 1ull);
-  const volatile Flags* vf = s.flags;
-  const int vfull = vf->v_full;
-  const int n = s.n;
-  double v2 = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double f[3];
-    if (s.precision == GBMD_FP64) {
-      double4_32a F = s.f64[i];
-      f[0] = F.x; f[1] = F.y; f[2] = F.z;
-    } else {
-      float4 F = s.f32[i];
-      f[0] = F.x; f[1] = F.y; f[2] = F.z;
-    }
-    for (int a = 0; a < 3; ++a) {
-      double v = s.v[a * n + i];
-      if (!vfull) v = fma(s.h, f[a], v);
-      v2 += v * v;
-    }
-  }
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int k = threadIdx.x; k < s.tile_count_f; k += blockDim.x) {
     const double* p = s.partials + 8 * (size_t)(s.tile_first_f + k);
-    for (int c = 0; c < 7; ++c) acc[c] += p[c];
+    for (int c = 0; c < 8; ++c) acc[c] += p[c];
   }
-  double r = block_sum<double>(v2, sh);
+  double r = block_sum<double>(acc[7], sh);
   if (threadIdx.x == 0) s.thermo[1] = r;
   for (int c = 0; c < 7; ++c) {
     r = block_sum<double>(acc[c], sh);
