@@ -240,7 +240,7 @@ std::vector<KernelCall> rebuild_calls(const Group* g) {
             cellsort_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl),
             permute_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
             copyback_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
-            nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi)};
+            nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi, g->ntbk > 0)};
   return {bin_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
           scan_call(g->d_desc, g->d_ts, g->nts, g->d_ctl),
           scatter_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
@@ -248,7 +248,7 @@ std::vector<KernelCall> rebuild_calls(const Group* g) {
           permute_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
           copyback_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
           blocks_call(g->d_desc, g->d_tbk, g->ntbk, g->d_ctl),
-          nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi)};
+          nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi, g->ntbk > 0)};
 }
 
 KernelCall step_force_call(const Group* g, int ev, int force_all) {

@@ -302,7 +302,7 @@ __device__ __forceinline__ int cell_centre_fixed(int c, int nc) {
 // of the centre).  With 1 or 2 cells on an axis a neighbour may sit on either side,
 // so the !REL variant keeps fixed-point coordinates and takes the minimum image
 // per test.
-template <bool MULTI, bool REL>
+template <bool MULTI, bool REL, bool STAGED>
 __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* __restrict__ sysv,
                                                                   const Tile* __restrict__ tiles,
                                                                   GroupCtl* ctl) {
@@ -315,8 +315,16 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   // r_list^2 (1 -+ band) per type pair (FP32)
   __shared__ float thr_lo[CELLS_PER_TILE][MAXT2], thr_hi[CELLS_PER_TILE][MAXT2];
   __shared__ double rl2d[CELLS_PER_TILE][MAXT2];
-  __shared__ float4 cand[CELLS_PER_TILE][32];
-  __shared__ int cand_l[CELLS_PER_TILE][32];   // staged: window-local index of the candidate
+  // the chunk of 32 candidates, one array per component so that candidates k and
+  // k + 1 load as one FP32x2 operand: x, y, z (relative to the cell centre; raw
+  // fixed point without REL), the type as 0/1, and j | type << 30
+  __shared__ __align__(8) float cxs[CELLS_PER_TILE][32], cys[CELLS_PER_TILE][32],
+      czs[CELLS_PER_TILE][32], cts[CELLS_PER_TILE][32];
+  __shared__ int cjs[CELLS_PER_TILE][32];
+  __shared__ int cand_l[STAGED ? CELLS_PER_TILE : 1][32];   // window-local index
+  // STAGED: some member of the group may use the staged force path (decided per
+  // system below); otherwise none does
+  const bool staged = STAGED && s.staged != 0;   // then every axis has >= 4 cells
   for (int k = lane; k < nt * nt; k += 32) {
     const float rl2 = s.pf[k].rl2;
     thr_lo[w][k] = rl2 * (1.0f - NL_BAND);
@@ -336,8 +344,6 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   const int lo2 = nc2 >= 3 ? -1 : 0, n2 = nc2 >= 3 ? 3 : nc2;
   const int nsc = n0 * n1 * n2;   // <= 27
   int sc_start = 0, sc_cnt = 0, sc_woff = 0;
-  const bool staged = s.staged != 0;   // then every axis has >= 4 cells (lo = -1)
-  const int blk = ((cz >> 1) * s.nb[1] + (cy >> 1)) * s.nb[0] + (cx >> 1);
   if (lane < nsc) {
     const int dx = lo0 + lane % n0, dy = lo1 + (lane / n0) % n1, dz = lo2 + lane / (n0 * n1);
     const int x = (cx + dx + nc0) % nc0, y = (cy + dy + nc1) % nc1, z = (cz + dz + nc2) % nc2;
@@ -345,6 +351,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     sc_start = s.cell_start[nr];
     sc_cnt = s.cell_start[nr + 1] - sc_start;
     if (staged) {   // this stencil cell's place in the block's 4x4x4 window
+      const int blk = ((cz >> 1) * s.nb[1] + (cy >> 1)) * s.nb[0] + (cx >> 1);
       const int wi = (((cz & 1) + 1 + dz) * 4 + ((cy & 1) + 1 + dy)) * 4 + ((cx & 1) + 1 + dx);
       sc_woff = s.blk_win[(size_t)blk * WIN_CELLS + wi].y;
     }
@@ -360,11 +367,14 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   const int cap = s.cap;
   const int* __restrict__ members = s.members;
   const int4* __restrict__ qv = s.q;
+  const bool two = !MULTI || nt <= 2;
   __syncwarp();
 
-  // candidate c of the flattened stream, relative to the cell centre; every lane
-  // runs every shuffle
-  auto fetch = [&](int c, int& local) -> float4 {
+  // candidate c of the flattened stream into registers (every lane runs every
+  // shuffle); written to the chunk arrays by stage() once the previous chunk is done
+  int4 nq = make_int4(0, 0, 0, -1);
+  int nloc = 0;
+  auto fetch = [&](int c) {
     int lo = 0;
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1) {
@@ -374,15 +384,29 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     }
     const int st = __shfl_sync(0xffffffffu, sc_start, lo);
     const int ex = __shfl_sync(0xffffffffu, excl, lo);
-    local = __shfl_sync(0xffffffffu, sc_woff, lo) + (c - ex);
-    if (c >= total) return make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    if (STAGED) nloc = __shfl_sync(0xffffffffu, sc_woff, lo) + (c - ex);
+    if (c >= total) {
+      nq = make_int4(0, 0, 0, -1);
+      return;
+    }
     const int j = members[st + (c - ex)];
     const int4 qj = qv[j];
-    if (!REL)
-      return make_float4(__int_as_float(qj.x), __int_as_float(qj.y), __int_as_float(qj.z),
-                         __int_as_float(j | (qj.w << NL_TYPE_SHIFT)));
-    return make_float4((float)min_image_fixed(qj.x, ox) * fs0, (float)min_image_fixed(qj.y, oy) * fs1,
-                       (float)min_image_fixed(qj.z, oz) * fs2, __int_as_float(j | (qj.w << NL_TYPE_SHIFT)));
+    nq = make_int4(qj.x, qj.y, qj.z, j | (qj.w << NL_TYPE_SHIFT));
+  };
+  auto stage = [&]() {
+    if (REL) {   // an empty slot sits far away: never within range
+      const bool none = nq.w < 0;
+      cxs[w][lane] = none ? 1e18f : (float)min_image_fixed(nq.x, ox) * fs0;
+      cys[w][lane] = none ? 1e18f : (float)min_image_fixed(nq.y, oy) * fs1;
+      czs[w][lane] = none ? 1e18f : (float)min_image_fixed(nq.z, oz) * fs2;
+      cts[w][lane] = (float)(((unsigned)nq.w >> NL_TYPE_SHIFT) & 1u);
+    } else {
+      cxs[w][lane] = __int_as_float(nq.x);
+      cys[w][lane] = __int_as_float(nq.y);
+      czs[w][lane] = __int_as_float(nq.z);
+    }
+    cjs[w][lane] = nq.w;
+    if (STAGED) cand_l[w][lane] = nloc;
   };
 
   unsigned long long nb_sum = 0;
@@ -393,74 +417,79 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     const float xi = (float)min_image_fixed(qi.x, ox) * fs0;
     const float yi = (float)min_image_fixed(qi.y, oy) * fs1;
     const float zi = (float)min_image_fixed(qi.z, oz) * fs2;
-    const float2 nxy = make_float2(-xi, -yi);
-    // squared list range by candidate type, widened by the relative band: the test
-    // loop keeps every candidate below hi = r_list^2 (1 + band) in a bit mask; the
-    // hits are then appended in order, the ones above r_list^2 (1 - band) after an
-    // FP64 decision.  Two types in registers; more types read the table.  An idle
-    // lane gets -1 (never keeps).
+    const float2 nX = make_float2(-xi, -xi), nY = make_float2(-yi, -yi), nZ = make_float2(-zi, -zi);
+    // the test keeps every candidate with r^2 below hi = r_list^2 (1 + band) in a bit
+    // mask (the sign bit of r^2 - hi); the hits are then appended in order, the ones
+    // above r_list^2 (1 - band) after an FP64 decision.  Two types: -hi for a type-0
+    // candidate and its change for type 1 in registers; more types read the table.
+    // An idle lane gets hi = -1 (never keeps).
     const int pt = MULTI ? qi.w * nt : 0;
     const float hi0 = valid ? thr_hi[w][pt] : -1.0f;
     const float hi1 = valid && MULTI ? thr_hi[w][pt + min(1, nt - 1)] : hi0;
-    const bool two = !MULTI || nt <= 2;
+    const float2 nh0 = make_float2(-hi0, -hi0), ndh = make_float2(hi0 - hi1, hi0 - hi1);
     int* __restrict__ nl = s.nl;
     const int stride = s.nl_stride;
     const int i_row = valid ? i : 0;
     int cnt = 0;
     const int m_row = ibase + lane;   // member rank (staged list rows)
     unsigned short* __restrict__ nl16 = reinterpret_cast<unsigned short*>(s.nl);
-    int next_l = 0;
-    float4 next = fetch(lane, next_l);
+    fetch(lane);
     for (int cb = 0; cb < total; cb += 32) {
-      cand[w][lane] = next;
-      cand_l[w][lane] = next_l;
+      stage();
       __syncwarp();
-      if (cb + 32 < total) next = fetch(cb + 32 + lane, next_l);   // in flight during the tests
-      const int m = min(32, total - cb);
+      if (cb + 32 < total) fetch(cb + 32 + lane);   // in flight during the tests
       unsigned mask = 0;
-      auto test = [&](int k) {
-        const float4 c = cand[w][k];
-        float r2;   // exactly 0 for the particle itself (dropped below)
-        if (REL) {
-          const float2 dxy = __fadd2_rn(make_float2(c.x, c.y), nxy);
-          const float dz = c.z - zi;
-          const float2 sq = __fmul2_rn(dxy, dxy);
-          r2 = fmaf(dz, dz, sq.x + sq.y);
-        } else {
-          const float dx = (float)min_image_fixed(qi.x, __float_as_int(c.x)) * fs0;
-          const float dy = (float)min_image_fixed(qi.y, __float_as_int(c.y)) * fs1;
-          const float dz = (float)min_image_fixed(qi.z, __float_as_int(c.z)) * fs2;
-          r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        }
-        float hi;
-        if (!MULTI) hi = hi0;
-        else if (two) hi = ((__float_as_int(c.w) >> NL_TYPE_SHIFT) & 1) ? hi1 : hi0;
-        else hi = valid ? thr_hi[w][pt + ((unsigned)__float_as_int(c.w) >> NL_TYPE_SHIFT)] : -1.0f;
-        return r2 < hi;
-      };
-      if (m == 32) {
+      if (REL) {
+        // candidates k, k + 1 at once in packed FP32x2
 #pragma unroll
-        for (int k = 0; k < 32; ++k) mask |= test(k) ? (1u << k) : 0u;
+        for (int k = 0; k < 32; k += 2) {
+          const float2 X = *reinterpret_cast<const float2*>(&cxs[w][k]);
+          const float2 Y = *reinterpret_cast<const float2*>(&cys[w][k]);
+          const float2 Z = *reinterpret_cast<const float2*>(&czs[w][k]);
+          float2 d;
+          if (!MULTI) {
+            d = nh0;
+          } else if (two) {
+            d = __ffma2_rn(*reinterpret_cast<const float2*>(&cts[w][k]), ndh, nh0);
+          } else {
+            const unsigned t0 = (unsigned)cjs[w][k] >> NL_TYPE_SHIFT;
+            const unsigned t1 = (unsigned)cjs[w][k + 1] >> NL_TYPE_SHIFT;
+            d = valid ? make_float2(-thr_hi[w][pt + (t0 & 3)], -thr_hi[w][pt + (t1 & 3)])
+                      : make_float2(1.0f, 1.0f);
+          }
+          const float2 dx = __fadd2_rn(X, nX), dy = __fadd2_rn(Y, nY), dz = __fadd2_rn(Z, nZ);
+          d = __ffma2_rn(dx, dx, d);
+          d = __ffma2_rn(dy, dy, d);
+          d = __ffma2_rn(dz, dz, d);
+          mask |= ((__float_as_uint(d.x) >> 31) << k) | ((__float_as_uint(d.y) >> 31) << (k + 1));
+        }
       } else {
-        for (int k = 0; k < m; ++k) mask |= test(k) ? (1u << k) : 0u;
+        const int m = min(32, total - cb);
+        for (int k = 0; k < m; ++k) {
+          const float dx = (float)min_image_fixed(qi.x, __float_as_int(cxs[w][k])) * fs0;
+          const float dy = (float)min_image_fixed(qi.y, __float_as_int(cys[w][k])) * fs1;
+          const float dz = (float)min_image_fixed(qi.z, __float_as_int(czs[w][k])) * fs2;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const unsigned ct = (unsigned)cjs[w][k] >> NL_TYPE_SHIFT;
+          const float hi = !MULTI ? hi0 : two ? ((ct & 1) ? hi1 : hi0)
+                                              : (valid ? thr_hi[w][pt + ct] : -1.0f);
+          mask |= (r2 < hi ? 1u : 0u) << k;
+        }
       }
       while (mask) {   // about a tenth of the candidates
         const int k = __ffs(mask) - 1;
         mask &= mask - 1;
-        const float4 c = cand[w][k];
-        const int cw = __float_as_int(c.w);
+        const int cw = cjs[w][k];
         const int j = cw & ((1 << NL_TYPE_SHIFT) - 1);
         if (j == i) continue;
         float r2;
         if (REL) {
-          const float2 dxy = __fadd2_rn(make_float2(c.x, c.y), nxy);
-          const float dz = c.z - zi;
-          const float2 sq = __fmul2_rn(dxy, dxy);
-          r2 = fmaf(dz, dz, sq.x + sq.y);
+          const float dx = cxs[w][k] - xi, dy = cys[w][k] - yi, dz = czs[w][k] - zi;
+          r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         } else {
-          const float dx = (float)min_image_fixed(qi.x, __float_as_int(c.x)) * fs0;
-          const float dy = (float)min_image_fixed(qi.y, __float_as_int(c.y)) * fs1;
-          const float dz = (float)min_image_fixed(qi.z, __float_as_int(c.z)) * fs2;
+          const float dx = (float)min_image_fixed(qi.x, __float_as_int(cxs[w][k])) * fs0;
+          const float dy = (float)min_image_fixed(qi.y, __float_as_int(cys[w][k])) * fs1;
+          const float dz = (float)min_image_fixed(qi.z, __float_as_int(czs[w][k])) * fs2;
           r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         }
         const int p = MULTI ? pt + ((unsigned)cw >> NL_TYPE_SHIFT) : 0;
@@ -504,9 +533,13 @@ SIMPLE_CALL(blocks_call, k_blocks, 256)
 #undef SIMPLE_CALL
 
 KernelCall nlist_call(const SysDev* d, const Tile* tl, int ntiles, GroupCtl* ctl, bool rel,
-                      bool multi) {
-  void* f = multi ? (rel ? (void*)k_nlist<true, true> : (void*)k_nlist<true, false>)
-                  : (rel ? (void*)k_nlist<false, true> : (void*)k_nlist<false, false>);
+                      bool multi, bool staged) {
+  void* const fs[2][2][2] = {
+      {{(void*)k_nlist<false, false, false>, (void*)k_nlist<false, false, true>},
+       {(void*)k_nlist<false, true, false>, (void*)k_nlist<false, true, true>}},
+      {{(void*)k_nlist<true, false, false>, (void*)k_nlist<true, false, true>},
+       {(void*)k_nlist<true, true, false>, (void*)k_nlist<true, true, true>}}};
+  void* f = fs[multi ? 1 : 0][rel ? 1 : 0][staged ? 1 : 0];
   KernelCall k = make_call(f, ntiles, CELLS_PER_TILE * 32, 0);
   put(k, d); put(k, tl); put(k, ctl);
   return k;

@@ -41,7 +41,7 @@ KernelCall copyback_call(const SysDev* d, const Tile* tiles_p, int ntiles, Group
 // window table of every staged 2x2x2 block (8 blocks per kernel block of 256)
 KernelCall blocks_call(const SysDev* d, const Tile* tiles_b, int ntiles, GroupCtl* ctl);
 KernelCall nlist_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl* ctl, bool rel,
-                      bool multi);
+                      bool multi, bool staged);
 // pair force (K5): ev = 0 forces only, 1 also energy/virial partial sums
 // (+ per-particle arrays when the descriptor has them); force_all ignores the
 // per-step activity flag (used outside the step graph)

@@ -99,7 +99,9 @@ def test_forces_energy_virial_at_creation(prec, case):
 def test_neighbor_sets_match_brute_force(prec):
     for w in (wl.lj_fluid(1500, 0.84, 1.2, seed=41),
               wl.lj_fluid(1200, 1.2, 1.0, seed=42, binary=True, r_buff=0.3),
-              wl.lj_fluid(256, 0.9, 1.2, seed=43)):          # 2 cells per axis
+              wl.lj_fluid(256, 0.9, 1.2, seed=43),            # 2 cells per axis
+              wl.lj_fluid(5000, 0.84, 1.2, seed=44),          # 6 cells: two-cell warps
+              wl.lj_fluid(5000, 1.2, 1.0, seed=45, binary=True, r_buff=0.3)):  # 5: odd
         s = gbmd.System.from_workload(w, precision=prec)
         for rnd in range(2):
             pos = s.state()[0]
