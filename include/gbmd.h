@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define GBMD_ABI_VERSION 2
+#define GBMD_ABI_VERSION 3
 #define GBMD_MAX_TYPES 4
 
 typedef enum gbmd_status {
@@ -138,6 +138,7 @@ typedef struct gbmd_info {
                                      cell blocks with their 4x4x4-cell neighbourhood in
                                      shared memory, 16-bit window-local indices) */
     int32_t max_window;           /* largest staged window at the last build (particles) */
+    double cell_scale;            /* cells are at least cell_scale * r_list,max wide */
 } gbmd_info;
 
 typedef struct gbmd_system gbmd_system;
@@ -231,11 +232,22 @@ int64_t gbmd_footprint_bytes(const gbmd_desc *d);
  * (-1 = no limit).  Steps asked beyond the limit are skipped on the device. */
 int gbmd_set_step_limit(gbmd_system *s, int64_t step);
 
-/* Choose the force kernel's threads per particle and block size by timing the
- * candidates on this system's current state; with a non-NULL cache_path the
- * choice is read from / appended to that text file, keyed by precision, type
- * count, size and density class. */
+/* Autotuner (Section 5: kernel parameters are tuned on the device at run time).
+ * Chooses, by timing the candidates on this system's current state: the cell
+ * width (a list rebuild at cells of 1, 1.1, 1.2 and 1.35 times r_list,max; kept
+ * at 1 on the staged force path), then the force kernel's threads per particle
+ * (1, 2, 4) and block size (128, 256, 512).  With a non-NULL cache_path the
+ * choice is read from / appended to that text file (one line per shape: key,
+ * threads per particle, block, cell scale), keyed by device, precision, type
+ * mode, size and density class. */
 int gbmd_autotune(gbmd_system *s, const char *cache_path);
+
+/* Cells at least `scale` * r_list,max wide (1 <= scale <= 4; the cell list of
+ * Listing 1's md.nlist.cell).  Rebuilds the cell grid, re-sorts into its Morton
+ * order and rebuilds the lists and forces at the current positions; neighbour
+ * sets are unchanged, the order of a particle's neighbours (and so the last bits
+ * of its FP32 force) may change.  GBMD_ERR_BAD_ARG outside [1, 4]. */
+int gbmd_set_cell_scale(gbmd_system *s, double scale);
 
 /* Set the force kernel's threads per particle (1, 2 or 4) and block size
  * (32..512, a multiple of 32) explicitly. */

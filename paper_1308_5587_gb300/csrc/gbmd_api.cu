@@ -72,6 +72,9 @@ struct gbmd_system {
   int batch_slot = -1;
   long long target_step = 0;  // steps requested so far (absolute), host bookkeeping
   long long step_limit = -1;
+  double rl_max = 0;          // largest r_list: the smallest allowed cell width
+  double cell_scale = 1.0;    // cell width >= cell_scale * rl_max (autotuned)
+  bool want_staged = false;   // GBMD_PATH_STAGED requested
   // staging for import/export (device)
   double *d_pos = nullptr, *d_vel = nullptr, *d_frc = nullptr;
   int *d_img = nullptr, *d_type = nullptr, *d_misc = nullptr;
@@ -515,6 +518,13 @@ struct Geometry {
   double rl_max;
 };
 
+// cells per axis: as many as fit with a width of at least scale * r_list,max (the
+// 27-cell stencil then holds every neighbour), at most 1024
+int cells_along(double L, double rl_max, double scale) {
+  const int c = (int)std::floor(L / (rl_max * scale * (1.0 + 1e-6)));
+  return std::min(std::max(c, 1), 1024);
+}
+
 Geometry geometry(const gbmd_desc* d) {
   Geometry g;
   const int nt = d->ntypes;
@@ -523,8 +533,7 @@ Geometry geometry(const gbmd_desc* d) {
   g.rl_max = rmax + d->r_buff;
   g.ncells = 1;
   for (int a = 0; a < 3; ++a) {
-    int c = (int)std::floor(d->box[a] / (g.rl_max * (1.0 + 1e-6)));
-    g.nc[a] = std::min(std::max(c, 1), 1024);
+    g.nc[a] = cells_along(d->box[a], g.rl_max, 1.0);
     g.ncells *= g.nc[a];
   }
   if (d->nlist_capacity > 0) {
@@ -565,6 +574,82 @@ size_t footprint_of(const gbmd_desc* d, const Geometry& g) {
   return b;
 }
 
+// staged force path possible: mixed precision, >= 4 cells per axis, expected windows
+// well inside shared memory (a larger one at a rebuild falls back, see sync_system)
+bool staged_ok(const SysDev& h, const int nc[3]) {
+  const double per_cell = (double)h.n / ((double)nc[0] * nc[1] * nc[2]);
+  return h.precision == GBMD_MIXED && nc[0] >= 4 && nc[1] >= 4 && nc[2] >= 4 &&
+         WIN_CELLS * per_cell * 1.35 + 96 <= STAGED_WINDOW_CAP;
+}
+
+void dfree(gbmd_system* s, void* p, size_t bytes) {
+  if (!p) return;
+  auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
+  if (it != s->allocs.end()) {
+    s->allocs.erase(it);
+    s->footprint -= std::max<size_t>(bytes, 16);
+  }
+  cudaFree(p);
+}
+
+// The cell grid: nc cells per axis, the arrays sized by the cell count and the
+// Morton rank of every cell.  Replaces an existing grid (its arrays are freed).
+int setup_cells(gbmd_system* s, const int nc[3], cudaStream_t st) {
+  SysDev& h = s->h;
+  CK(cudaStreamSynchronize(st));
+  if (h.cell_cnt) {
+    const size_t oc = (size_t)h.ncells, ob = (size_t)h.nblocks;
+    dfree(s, h.cell_cnt, (oc + 1) * 4); dfree(s, h.cell_start, (oc + 1) * 4);
+    dfree(s, h.cell_cursor, (oc + 1) * 4);
+    dfree(s, const_cast<int*>(h.rank2lin), oc * 4); dfree(s, const_cast<int*>(h.lin2rank), oc * 4);
+    dfree(s, h.blk_win, ob * WIN_CELLS * sizeof(int2)); dfree(s, h.blk_info, ob * sizeof(int4));
+    h.cell_cnt = h.cell_start = h.cell_cursor = nullptr;
+    h.rank2lin = h.lin2rank = nullptr;
+    h.blk_win = nullptr;
+    h.blk_info = nullptr;
+  }
+  int ncells = 1, nblocks = 1;
+  for (int a = 0; a < 3; ++a) {
+    h.nc[a] = nc[a];
+    ncells *= nc[a];
+    h.nb[a] = (nc[a] + 1) / 2;
+    nblocks *= h.nb[a];
+  }
+  h.ncells = ncells;
+  h.nblocks = nblocks;
+  int rc = GBMD_OK;
+  auto A = [&](void** p, size_t bytes) {
+    if (rc == GBMD_OK) rc = dalloc(s, p, bytes);
+  };
+  A((void**)&h.blk_win, (size_t)nblocks * WIN_CELLS * sizeof(int2));
+  A((void**)&h.blk_info, (size_t)nblocks * sizeof(int4));
+  A((void**)&h.cell_cnt, ((size_t)ncells + 1) * 4); A((void**)&h.cell_start, ((size_t)ncells + 1) * 4);
+  A((void**)&h.cell_cursor, ((size_t)ncells + 1) * 4);
+  int *r2l = nullptr, *l2r = nullptr;
+  A((void**)&r2l, (size_t)ncells * 4); A((void**)&l2r, (size_t)ncells * 4);
+  h.rank2lin = r2l;
+  h.lin2rank = l2r;
+  if (rc != GBMD_OK) return rc;
+  std::vector<std::pair<uint32_t, int>> code(ncells);
+  for (int z = 0; z < nc[2]; ++z)
+    for (int y = 0; y < nc[1]; ++y)
+      for (int x = 0; x < nc[0]; ++x) {
+        const int lin = (z * nc[1] + y) * nc[0] + x;
+        code[lin] = {spread3(x) | (spread3(y) << 1) | (spread3(z) << 2), lin};
+      }
+  std::sort(code.begin(), code.end());
+  std::vector<int> rl(ncells), lr(ncells);
+  for (int r = 0; r < ncells; ++r) {
+    rl[r] = code[r].second;
+    lr[code[r].second] = r;
+  }
+  CK(cudaMemcpyAsync(r2l, rl.data(), (size_t)ncells * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(l2r, lr.data(), (size_t)ncells * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(h.cell_cnt, 0, ((size_t)ncells + 1) * 4, st));
+  CK(cudaStreamSynchronize(st));   // the host tables die here
+  return GBMD_OK;
+}
+
 int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   if (!out) return fail(GBMD_ERR_BAD_ARG, "out is NULL");
   *out = nullptr;
@@ -590,26 +675,15 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   h.dt = d->dt;
   h.mass = d->mass;
   h.h = 0.5 * d->dt / d->mass;
-  h.ncells = geo.ncells;
-  h.nblocks = 1;
-  for (int a = 0; a < 3; ++a) {
-    h.nb[a] = (geo.nc[a] + 1) / 2;
-    h.nblocks *= h.nb[a];
-  }
-  // staged force path: mixed precision, >= 4 cells per axis, expected windows well
-  // inside shared memory (a larger one at a rebuild falls back, see sync_system)
-  {
-    const double per_cell = (double)n / geo.ncells;
-    h.staged = d->force_path == GBMD_PATH_STAGED && d->precision == GBMD_MIXED && geo.nc[0] >= 4 && geo.nc[1] >= 4 &&
-               geo.nc[2] >= 4 && WIN_CELLS * per_cell * 1.35 + 96 <= STAGED_WINDOW_CAP;
-    h.window_cap = STAGED_WINDOW_CAP;
-  }
+  s->rl_max = geo.rl_max;
+  s->want_staged = d->force_path == GBMD_PATH_STAGED;
+  h.staged = s->want_staged && staged_ok(h, geo.nc);
+  h.window_cap = STAGED_WINDOW_CAP;
   for (int a = 0; a < 3; ++a) {
     h.L[a] = d->box[a];
     h.halfL[a] = 0.5 * d->box[a];
     h.qscale[a] = 4294967296.0 / d->box[a];
     h.fscale[a] = (float)(d->box[a] / 4294967296.0);
-    h.nc[a] = geo.nc[a];
   }
   const double hb = 0.5 * d->r_buff;
   h.rbuff_half2 = (float)(hb * hb * (1.0 - 1e-5));
@@ -649,13 +723,6 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   A((void**)&h.nn, N * 4); A((void**)&h.nl, round_up(N, 32) * 4 * (size_t)geo.cap);
   A((void**)&h.key, N * 4); A((void**)&h.members, N * 4); A((void**)&h.members_tmp, N * 4);
   A((void**)&h.rmember, N * 4);
-  A((void**)&h.blk_win, (size_t)h.nblocks * WIN_CELLS * sizeof(int2));
-  A((void**)&h.blk_info, (size_t)h.nblocks * sizeof(int4));
-  A((void**)&h.cell_cnt, (geo.ncells + 1) * 4); A((void**)&h.cell_start, (geo.ncells + 1) * 4);
-  A((void**)&h.cell_cursor, (geo.ncells + 1) * 4);
-  int *r2l = nullptr, *l2r = nullptr;
-  A((void**)&r2l, geo.ncells * 4); A((void**)&l2r, geo.ncells * 4);
-  h.rank2lin = r2l; h.lin2rank = l2r;
   A((void**)&h.x_alt, N * 24); A((void**)&h.v_alt, N * 24); A((void**)&h.img_alt, N * 12);
   A((void**)&h.type_alt, N * 4); A((void**)&h.tag_alt, N * 4); A((void**)&h.q_alt, N * 16);
   A((void**)&h.thermo, 16 * 8);
@@ -666,28 +733,13 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   s->d_thermo = h.thermo;
   if (rc != GBMD_OK) { gbmd_destroy(s); return rc; }
   cudaStream_t st = s->stream;
-  // Morton rank of every cell
+  rc = setup_cells(s, geo.nc, st);
+  if (rc != GBMD_OK) { std::string m = g_err; gbmd_destroy(s); g_err = m; return rc; }
   {
-    std::vector<std::pair<uint32_t, int>> code(geo.ncells);
-    for (int z = 0; z < geo.nc[2]; ++z)
-      for (int y = 0; y < geo.nc[1]; ++y)
-        for (int x = 0; x < geo.nc[0]; ++x) {
-          const int lin = (z * geo.nc[1] + y) * geo.nc[0] + x;
-          code[lin] = {spread3(x) | (spread3(y) << 1) | (spread3(z) << 2), lin};
-        }
-    std::sort(code.begin(), code.end());
-    std::vector<int> rl(geo.ncells), lr(geo.ncells);
-    for (int r = 0; r < geo.ncells; ++r) {
-      rl[r] = code[r].second;
-      lr[code[r].second] = r;
-    }
-    cudaError_t e1 = cudaMemcpyAsync(r2l, rl.data(), geo.ncells * 4, cudaMemcpyHostToDevice, st);
-    cudaError_t e2 = cudaMemcpyAsync(l2r, lr.data(), geo.ncells * 4, cudaMemcpyHostToDevice, st);
-    cudaError_t e3 = cudaMemsetAsync(h.cell_cnt, 0, (geo.ncells + 1) * 4, st);
     cudaError_t e5 = cudaMemsetAsync(s->d_flags, 0, sizeof(Flags), st);
     cudaError_t e6 = cudaMemsetAsync(h.nn, 0, N * 4, st);
     cudaError_t e4 = cudaStreamSynchronize(st);
-    if (e1 || e2 || e3 || e4 || e5 || e6) { gbmd_destroy(s); return fail(GBMD_ERR_CUDA, "uploading the cell tables failed"); }
+    if (e4 || e5 || e6) { gbmd_destroy(s); return fail(GBMD_ERR_CUDA, "clearing the flags failed"); }
   }
   // own group
   s->own = new Group();
@@ -828,6 +880,84 @@ int time_force(Group* g, float* ms) {
   return GBMD_OK;
 }
 
+// Cells at least scale * r_list,max wide: a new cell grid, then the lists (with a
+// re-sort into the new Morton order) and the forces at the current positions.  The
+// neighbour sets do not change (r_list does not); the order of a particle's
+// neighbours, and so the FP32 summation order of its force, may.
+int regrid(gbmd_system* s, double scale) {
+  if (!(scale >= 1.0 && scale <= 4.0)) return fail(GBMD_ERR_BAD_ARG, "cell scale must be in [1, 4]");
+  SysDev& h = s->h;
+  int nc[3];
+  for (int a = 0; a < 3; ++a) nc[a] = cells_along(h.L[a], s->rl_max, scale);
+  s->cell_scale = scale;
+  if (nc[0] == h.nc[0] && nc[1] == h.nc[1] && nc[2] == h.nc[2]) return GBMD_OK;
+  RET(sync_system(s));   // nothing in flight, nothing owed
+  cudaStream_t st = cur_stream(s);
+  RET(setup_cells(s, nc, st));
+  h.staged = s->want_staged && staged_ok(h, nc);
+  RET(refresh_desc(s));
+  for (int round = 0; round < 2; ++round) {
+    Flags f;
+    RET(read_flags(s, &f, st));
+    if (round == 1 && f.error != DEV_WINDOW) break;
+    if (f.error == DEV_WINDOW) {   // a staged window outgrew shared memory
+      h.staged = 0;
+      RET(refresh_desc(s));
+      f.error = 0;
+    }
+    f.do_rebuild = 1;
+    f.do_sort = 1;
+    f.last_sort = f.step;
+    f.n_sorts += 1;
+    RET(write_flags(s, &f, st));
+    RET(rebuild_and_force(s, 0));
+    CK(cudaStreamSynchronize(st));
+  }
+  Flags f;
+  RET(read_flags(s, &f, st));
+  if (f.error) return fail(GBMD_ERR_STATE, "device error %d after a new cell grid", f.error);
+  f.do_rebuild = 0;
+  f.do_sort = 0;
+  return write_flags(s, &f, st);
+}
+
+// Mean time of one full list rebuild (no re-sort) of every member of the group.
+int time_rebuild(Group* g, float* ms) {
+  RET(sync_layout(g));
+  std::vector<gbmd_system*> m = live(g);
+  for (auto* s : m) {
+    Flags f;
+    RET(read_flags(s, &f, g->stream));
+    f.do_rebuild = 1;
+    f.do_sort = 0;
+    RET(write_flags(s, &f, g->stream));
+  }
+  const std::vector<KernelCall> calls = rebuild_calls(g);
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  for (const KernelCall& c : calls) CK(launch(c, g->stream));
+  CK(cudaEventRecord(a, g->stream));
+  const int reps = 3;
+  for (int k = 0; k < reps; ++k)
+    for (const KernelCall& c : calls) CK(launch(c, g->stream));
+  CK(cudaEventRecord(b, g->stream));
+  CK(cudaEventSynchronize(b));
+  float t = 0;
+  CK(cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t / reps;
+  for (auto* s : m) {   // the lists stand for the current positions
+    Flags f;
+    RET(read_flags(s, &f, g->stream));
+    if (f.error) return fail(GBMD_ERR_STATE, "device error %d while timing a rebuild", f.error);
+    f.do_rebuild = 0;
+    RET(write_flags(s, &f, g->stream));
+  }
+  return GBMD_OK;
+}
+
 std::string tune_key(const Group* g) {
   std::vector<gbmd_system*> m = live(g);
   long long np = 0;
@@ -868,13 +998,46 @@ int autotune_group(Group* g, const char* cache) {
     std::ifstream in(cache);
     std::string line;
     int bt = 0, bb = 0;
+    double bs = 1.0;
     while (std::getline(in, line)) {
       std::istringstream ls(line);
       std::string k;
       int t, b;
-      if (ls >> k >> t >> b && k == key) { bt = t; bb = b; }
+      if (ls >> k >> t >> b && k == key) {
+        bt = t;
+        bb = b;
+        double sc;
+        bs = (ls >> sc) ? sc : 1.0;
+      }
     }
-    if (bt) return set_tuning(g, bt, bb);
+    if (bt) {
+      for (auto* s : live(g)) RET(regrid(s, bs));
+      return set_tuning(g, bt, bb);
+    }
+  }
+  // cell width: the list rebuild at each candidate width (the global force path does
+  // not depend on it); a wider cell only wins if it is clearly faster
+  double best_s = 1.0;
+  {
+    bool any_staged = false;
+    for (auto* s : live(g)) any_staged |= s->h.staged != 0;
+    if (!any_staged) {
+      float best_r = 1e30f;
+      std::vector<std::vector<int>> seen;
+      for (double sc : {1.0, 1.1, 1.2, 1.35}) {
+        std::vector<int> grid;
+        for (auto* s : live(g))
+          for (int a = 0; a < 3; ++a) grid.push_back(cells_along(s->h.L[a], s->rl_max, sc));
+        if (std::find(seen.begin(), seen.end(), grid) != seen.end()) continue;
+        seen.push_back(grid);
+        for (auto* s : live(g)) RET(regrid(s, sc));
+        float ms;
+        RET(time_rebuild(g, &ms));
+        if (getenv("GBMD_VERBOSE")) fprintf(stderr, "gbmd autotune %s cell_scale=%.2f rebuild %.4f ms\n", key.c_str(), sc, ms);
+        if (ms < 0.97f * best_r) { best_r = ms; best_s = sc; }
+      }
+      for (auto* s : live(g)) RET(regrid(s, best_s));
+    }
   }
   int best_t = g->tpp, best_b = g->fblock;
   float best = 1e30f;
@@ -889,7 +1052,7 @@ int autotune_group(Group* g, const char* cache) {
   RET(set_tuning(g, best_t, best_b));
   if (cache) {
     std::ofstream o(cache, std::ios::app);
-    o << key << " " << best_t << " " << best_b << "\n";
+    o << key << " " << best_t << " " << best_b << " " << best_s << "\n";
   }
   return GBMD_OK;
 }
@@ -1097,6 +1260,7 @@ int gbmd_get_info(gbmd_system* s, gbmd_info* out) {
   out->footprint_bytes = (int64_t)s->footprint;
   out->force_path = s->h.staged ? 1 : 0;
   out->max_window = f.max_window;
+  out->cell_scale = s->cell_scale;
   return GBMD_OK;
 }
 
@@ -1118,6 +1282,12 @@ int gbmd_set_step_limit(gbmd_system* s, int64_t step) {
   f.step_limit = step;
   s->step_limit = step;
   return write_flags(s, &f, st);
+}
+
+int gbmd_set_cell_scale(gbmd_system* s, double scale) {
+  if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
+  RET(use_device(s->device));
+  return regrid(s, scale);
 }
 
 int gbmd_set_force_events(gbmd_system* s, void* ev_begin, void* ev_end) {

@@ -65,7 +65,7 @@ class gbmd_info(C.Structure):
                 ("step", C.c_int64), ("n_rebuilds", C.c_int64), ("n_sorts", C.c_int64),
                 ("kernel_launches", C.c_int64), ("neighbors_total", C.c_int64),
                 ("footprint_bytes", C.c_int64), ("force_path", C.c_int32),
-                ("max_window", C.c_int32)]
+                ("max_window", C.c_int32), ("cell_scale", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +94,7 @@ _SIGS = {
     "gbmd_set_force_events": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gbmd_autotune": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gbmd_set_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "gbmd_set_cell_scale": (C.c_int, [C.c_void_p, C.c_double]),
     "gbmd_batch_create": (C.c_int, [C.c_int32, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "gbmd_batch_add": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "gbmd_batch_remove": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -296,6 +297,10 @@ def gbmd_set_tuning(h, tpp: int, block: int):
     return _check(load().gbmd_set_tuning(h, int(tpp), int(block)))
 
 
+def gbmd_set_cell_scale(h, scale: float):
+    return _check(load().gbmd_set_cell_scale(h, float(scale)))
+
+
 def gbmd_batch_create(precision, stream=None, cuda_device=-1) -> int:
     h = C.c_void_p()
     p = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
@@ -409,6 +414,9 @@ class System:
 
     def set_tuning(self, tpp: int, block: int):
         gbmd_set_tuning(self.handle, tpp, block)
+
+    def set_cell_scale(self, scale: float):
+        gbmd_set_cell_scale(self.handle, scale)
 
     def set_force_events(self, ev_begin, ev_end):
         gbmd_set_force_events(self.handle, ev_begin, ev_end)

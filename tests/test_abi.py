@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.gbmd_abi_version() == 2
+    assert lib.gbmd_abi_version() == 3
 
 
 def _desc(lib, **over):

@@ -403,3 +403,58 @@ def test_staged_window_overflow_falls_back():
     s.step(20)
     assert s.state()[3] == 20
     s.close()
+
+
+def _pairs_of(s, n):
+    counts, idx = s.neighbors(cap=512)
+    out = set()
+    for i in range(n):
+        for j in idx[i, :counts[i]]:
+            out.add((min(i, int(j)), max(i, int(j))))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cell_width_changes_nothing_physical(prec):
+    """Wider cells (gbmd_set_cell_scale): a new grid, the same neighbour sets, the
+    same forces up to summation order, and the same trajectory."""
+    w = wl.lj_fluid(5000, 0.84, 1.2, seed=61)
+    a = gbmd.System.from_workload(w, precision=prec)
+    b = gbmd.System.from_workload(w, precision=prec)
+    a.step(30)
+    b.step(30)
+    for x in (a, b):          # both rebuild their lists at the current positions
+        x.set_state(*x.state())
+    c0 = a.info()["cells"]
+    before = _pairs_of(a, w.n)
+    a.set_cell_scale(1.3)
+    info = a.info()
+    assert info["cell_scale"] == 1.3 and all(x < y for x, y in zip(info["cells"], c0))
+    assert _pairs_of(a, w.n) == before
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    assert rel_l2(a.forces(), b.forces()) <= tol
+    a.step(40)
+    b.step(40)
+    pa, pb = a.state()[0], b.state()[0]
+    assert np.abs(mi(pa - pb, w.box)).max() <= (1e-9 if prec == "fp64" else 1e-5)
+    Fo, Uo, _, _, _ = oracle.forces(pa, w.box, w.types, w.pairs.as_dict())
+    assert rel_l2(a.forces(), Fo) <= (1e-12 if prec == "fp64" else 1e-5)
+    with pytest.raises(gbmd.GbmdError):
+        a.set_cell_scale(0.5)
+    a.close()
+    b.close()
+
+
+def test_autotune_picks_a_valid_cell_width_and_tuning():
+    w = wl.lj_fluid(8000, 1.2, 1.0, seed=62, binary=True, r_buff=0.3)
+    s = gbmd.System.from_workload(w, precision="mixed")
+    s.step(20)
+    s.autotune(None)
+    info = s.info()
+    assert info["cell_scale"] in (1.0, 1.1, 1.2, 1.35)
+    assert info["threads_per_particle"] in (1, 2, 4) and info["force_block"] in (128, 256, 512)
+    s.step(20)
+    pos = s.state()[0]
+    Fo, _, _, _, _ = oracle.forces(pos, w.box, w.types, w.pairs.as_dict())
+    assert rel_l2(s.forces(), Fo) <= 1e-5
+    s.close()
