@@ -683,6 +683,7 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
     h.L[a] = d->box[a];
     h.halfL[a] = 0.5 * d->box[a];
     h.qscale[a] = 4294967296.0 / d->box[a];
+    h.dtq[a] = d->dt * h.qscale[a];
     h.fscale[a] = (float)(d->box[a] / 4294967296.0);
   }
   const double hb = 0.5 * d->r_buff;

@@ -81,6 +81,7 @@ struct SysDev {
   int *rmember;            // particle index -> member rank
   int sort_period;
   double dt, h;            // h = dt / (2 m)
+  double dtq[3];           // dt * 2^32 / L: the drift in box-fraction units
   double mass;
   // per type pair
   PairF pf[MAXT2];

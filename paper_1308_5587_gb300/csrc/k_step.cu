@@ -19,7 +19,32 @@ namespace gbmd {
 // ---------------------------------------------------------------------------
 // K6: kicks + drift + wrap + fixed-point shadow + displacement check, then the
 // last block of the grid makes the per-step decisions for every system.
+// FP64 runs at 1/64 of the FP32 rate on this part, so the kernel keeps the FP64
+// pipe to the six FMAs of the kicks and drifts plus one add per axis: the FP32
+// force is widened to FP64 with integer operations (IEEE-754 field by field), and
+// rint of the position uses the 1.5 * 2^52 rounding constant instead of a
+// conversion instruction.
 // ---------------------------------------------------------------------------
+
+// float -> double, exactly, on the integer pipe.  Zero and subnormal inputs (a
+// force below 1.2e-38) give zero; inf / NaN set `bad`.
+__device__ __forceinline__ double widen_f32(float f, bool& bad) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  bad |= ex == 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long mag = ((unsigned long long)(ex + 896u) << 52) |   // 1023 - 127
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)(sign | (ex ? mag : 0ull)));
+}
+
+// rint(x) (ties to even) as an integer for |x| < 2^51: x + 1.5 * 2^52 lies in
+// [2^52, 2^53), where the spacing of doubles is 1, so the sum is rounded to an
+// integer and its bit pattern minus the constant's is that integer
+__device__ __forceinline__ long long rint_ll(double x) {
+  const double m = x + 6755399441055744.0;
+  return __double_as_longlong(m) - 0x4338000000000000LL;
+}
 template <int PREC>
 __global__ void __launch_bounds__(TILE_P) k_integrate(const SysDev* __restrict__ sysv,
                                                       const Tile* __restrict__ tiles,
@@ -42,8 +67,8 @@ __global__ void __launch_bounds__(TILE_P) k_integrate(const SysDev* __restrict__
     const int n = s.n;
     double* __restrict__ xp = s.x;
     double* __restrict__ vp = s.v;
-    const double kick = vfull ? s.h : 2.0 * s.h;   // closing + opening half kicks
-    const double dtq[3] = {s.dt * s.qscale[0], s.dt * s.qscale[1], s.dt * s.qscale[2]};
+    const double kick = vfull ? s.h : s.h + s.h;   // closing + opening half kicks
+    const double dtq[3] = {s.dtq[0], s.dtq[1], s.dtq[2]};
     const float fsc[3] = {s.fscale[0], s.fscale[1], s.fscale[2]};
     const double Lr[3] = {s.L[0] * (1.0 / 4294967296.0), s.L[1] * (1.0 / 4294967296.0),
                           s.L[2] * (1.0 / 4294967296.0)};
@@ -57,7 +82,9 @@ __global__ void __launch_bounds__(TILE_P) k_integrate(const SysDev* __restrict__
       f[0] = F.x; f[1] = F.y; f[2] = F.z;
     } else {
       const float4 F = __ldg(s.f32 + i);
-      f[0] = F.x; f[1] = F.y; f[2] = F.z;
+      f[0] = widen_f32(F.x, bad);
+      f[1] = widen_f32(F.y, bad);
+      f[2] = widen_f32(F.z, bad);
     }
     double v[3], xq[3];
 #pragma unroll
@@ -73,7 +100,7 @@ __global__ void __launch_bounds__(TILE_P) k_integrate(const SysDev* __restrict__
     for (int a = 0; a < 3; ++a) {
       v[a] = fma(kick, f[a], v[a]);
       xq[a] = fma(dtq[a], v[a], xq[a]);
-      long long qq = __double2ll_rn(xq[a]);
+      long long qq = rint_ll(xq[a]);
       const long long k = (qq + 0x80000000LL) >> 32;       // floor((xq + 2^31) / 2^32)
       if (k != 0) {
         if (k > 1 || k < -1 || !isfinite(xq[a])) bad = true;
