@@ -21,6 +21,7 @@
 //               to 32, cap (a multiple of 4) entries per particle
 //   cell arrays key [N] (cell rank), cnt/start/cursor [ncells+1], members [N]
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -55,6 +56,33 @@ struct Flags {
   unsigned long long launches;   // kernels executed for this system
   unsigned long long nb_total;   // sum of neighbour counts at the last build
 };
+
+static_assert(sizeof(Flags) == 88 && offsetof(Flags, step) == 32, "Flags layout");
+
+// Device reads of a system's flags, which other blocks and kernels of the step
+// write: volatile vector loads, so that the fields a kernel needs arrive in one
+// round trip instead of one dependent load each.  Flags sit at the start of their
+// own cudaMalloc allocation (256-byte aligned).
+struct FlagWords {
+  int rebuild_req, do_rebuild, do_sort, active;   // bytes 0..15
+  int error, overflow_need, v_full, max_window;   // bytes 16..31
+};
+__device__ __forceinline__ FlagWords load_flag_words(const Flags* f) {
+  FlagWords w;
+  asm volatile("ld.volatile.global.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(w.rebuild_req), "=r"(w.do_rebuild), "=r"(w.do_sort), "=r"(w.active)
+               : "l"(f));
+  asm volatile("ld.volatile.global.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(w.error), "=r"(w.overflow_need), "=r"(w.v_full), "=r"(w.max_window)
+               : "l"(reinterpret_cast<const char*>(f) + 16));
+  return w;
+}
+// (step, step_limit) and (last_sort, n_rebuilds)
+__device__ __forceinline__ longlong2 load_flag_pair(const long long* p) {
+  longlong2 r;
+  asm volatile("ld.volatile.global.v2.s64 {%0, %1}, [%2];" : "=l"(r.x), "=l"(r.y) : "l"(p));
+  return r;
+}
 
 // pair coefficients: lj1 = 48 eps sigma^12, lj2 = 24 eps sigma^6 (force/r factors),
 // c12 = 4 eps sigma^12, c6 = 4 eps sigma^6, shift = V_LJ(r_cut)

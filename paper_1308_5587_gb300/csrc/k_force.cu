@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
   if (threadIdx.x == 0 && t.first == 0) atomicAdd(&s.flags->launches, 1ull);
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
   if (!force_all) {
-    const volatile Flags* vf = s.flags;
-    if (!vf->active || vf->error) return;   // uniform over the block
+    const FlagWords fw = load_flag_words(s.flags);
+    if (!fw.active || fw.error) return;   // uniform over the block
   }
   const int nt = s.ntypes;
   constexpr bool SMEM_TAB = PREC == GBMD_MIXED ? MT == 2 : MT != 0;
@@ -302,9 +302,9 @@ __global__ void __launch_bounds__(STAGED_BLOCK) k_force_staged(const SysDev* __r
   if (threadIdx.x == 0 && t.first == 0) atomicAdd(&s.flags->launches, 1ull);
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
   {
-    const volatile Flags* vf = s.flags;
-    if (vf->error) return;                  // e.g. a window too large: nothing is valid
-    if (!force_all && !vf->active) return;  // uniform over the block
+    const FlagWords fw = load_flag_words(s.flags);
+    if (fw.error) return;                   // e.g. a window too large: nothing is valid
+    if (!force_all && !fw.active) return;   // uniform over the block
   }
   const int b = t.first;
   const int4 info = s.blk_info[b];          // (first member, particles, window total, 0)

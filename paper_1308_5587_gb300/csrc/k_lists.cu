@@ -34,8 +34,8 @@ __device__ __forceinline__ bool rebuilding(const SysDev& s) {
   return ((const volatile Flags*)s.flags)->do_rebuild != 0;
 }
 __device__ __forceinline__ bool sorting(const SysDev& s) {
-  const volatile Flags* f = s.flags;
-  return f->do_rebuild != 0 && f->do_sort != 0;
+  const FlagWords w = load_flag_words(s.flags);
+  return w.do_rebuild != 0 && w.do_sort != 0;
 }
 __device__ __forceinline__ void count(const SysDev& s, const Tile& t, GroupCtl* ctl) {
   if (threadIdx.x == 0 && t.first == 0) atomicAdd(&s.flags->launches, 1ull);

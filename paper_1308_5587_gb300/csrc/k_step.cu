@@ -57,9 +57,10 @@ __global__ void __launch_bounds__(TILE_P) k_integrate(const SysDev* __restrict__
   Flags* fl = s.flags;
   if (threadIdx.x == 0 && t.first == 0) atomicAdd(&fl->launches, 1ull);
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
-  const volatile Flags* vf = fl;
-  const bool active = vf->error == 0 && (vf->step_limit < 0 || vf->step < vf->step_limit);
-  const int vfull = vf->v_full;
+  const FlagWords fw = load_flag_words(fl);
+  const longlong2 sl = load_flag_pair(&fl->step);   // (step, step_limit)
+  const bool active = fw.error == 0 && (sl.y < 0 || sl.x < sl.y);
+  const int vfull = fw.v_full;
 
   bool need = false, bad = false;
   const int i = t.first + threadIdx.x;
@@ -141,23 +142,27 @@ __global__ void __launch_bounds__(TILE_P) k_integrate(const SysDev* __restrict__
   __threadfence();
   int any = 0;
   for (int k = threadIdx.x; k < nsys; k += blockDim.x) {
-    volatile Flags* g = sysv[k].flags;
-    const bool act = g->error == 0 && (g->step_limit < 0 || g->step < g->step_limit);
+    Flags* gf = sysv[k].flags;
+    volatile Flags* g = gf;
+    // every field the decision needs, in flight together; then the stores
+    const FlagWords w = load_flag_words(gf);
+    const longlong2 sl = load_flag_pair(&gf->step);        // (step, step_limit)
+    const longlong2 lr = load_flag_pair(&gf->last_sort);   // (last_sort, n_rebuilds)
+    const long long nsort = g->n_sorts;
+    const int sp = sysv[k].sort_period;
+    const bool act = w.error == 0 && (sl.y < 0 || sl.x < sl.y);
     if (act) {
-      g->step = g->step + 1;
+      const long long st = sl.x + 1;
+      const int rb = w.rebuild_req;
+      const int srt = rb && sp > 0 && (st - lr.x >= sp);
+      g->step = st;
       g->v_full = 0;
-      const int rb = g->rebuild_req;
       g->rebuild_req = 0;
       g->do_rebuild = rb;
-      int srt = 0;
-      if (rb) {
-        g->n_rebuilds = g->n_rebuilds + 1;
-        const int sp = sysv[k].sort_period;
-        srt = sp > 0 && (g->step - g->last_sort >= sp);
-        if (srt) {
-          g->last_sort = g->step;
-          g->n_sorts = g->n_sorts + 1;
-        }
+      if (rb) g->n_rebuilds = lr.y + 1;
+      if (srt) {
+        g->last_sort = st;
+        g->n_sorts = nsort + 1;
       }
       g->do_sort = srt;
       g->active = 1;
