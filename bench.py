@@ -348,11 +348,16 @@ def gpu_arm(args):
     value = units / t_max
     ms_per_step = 1e3 * t_max / args.steps
 
-    # roofline of the dominant kernel (pair force): algorithmic bytes per launch
+    # roofline of the dominant kernel, the step kernel (pair force + integrate), in
+    # algorithmic bytes per launch and particle: the pair force's own shadow, count
+    # and indices (16 + 4 + 4 <n>; neighbour positions come from L1/L2) plus the
+    # integration's x, v read and written (96), build shadow read (16) and next
+    # shadow written (16); FP64 gathers a 32 B position and also writes its next one
     nbar = info["neighbors_total"] / n
-    f_bytes = 16 if precision == "mixed" else 32
-    pos_bytes = 16 if precision == "mixed" else 32
-    alg_bytes = n * (pos_bytes + 4 + 4 * nbar + f_bytes)
+    if precision == "mixed":
+        alg_bytes = n * (16 + 4 + 4 * nbar + 96 + 16 + 16)
+    else:
+        alg_bytes = n * (32 + 4 + 4 * nbar + 96 + 16 + 16 + 32)
     peak, peak_kind = measured_peaks()
     f_mean = float(force_ms.mean())
     achieved = alg_bytes / (f_mean * 1e-3) / 1e9
@@ -366,13 +371,10 @@ def gpu_arm(args):
                 "force_ms_mean": round(f_mean, 5), "peak_kind": f"of {peak_kind}",
                 "force_share_of_step": round(f_mean / float(step_ms.mean()), 3)}
 
-    # second line: the whole step.  Integrate reads F, v, x, type, x_build-shadow and
-    # writes v, x, the shadow (mixed 148 B/particle; FP64 adds 16 B of F and a 32 B
-    # FP64 shadow); each rebuild writes the list (4 <n>) and ~60 B of cell-list and
-    # count traffic per particle.
+    # second line: the whole step -- the step kernel plus the amortised rebuild, which
+    # writes the list (4 <n>) and ~60 B of cell-list and count traffic per particle
     reb = info["n_rebuilds"] / max(info["step"], 1)
-    int_bytes = 148 if precision == "mixed" else 196
-    step_bytes = alg_bytes + n * (int_bytes + reb * (60 + 4 * nbar))
+    step_bytes = alg_bytes + n * reb * (60 + 4 * nbar)
     step_achieved = step_bytes / (float(step_ms.mean()) * 1e-3) / 1e9
     roofline_step = {"bound": "hbm", "achieved": round(step_achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(step_achieved / peak, 4),
@@ -491,7 +493,7 @@ def batch_arm(args):
     assert all(math.isfinite(t["pe"]) for t in th)
     t_max = reduce_scalar(dist, float(step_ms.sum()) / 1e3, "max")
     value = reduce_scalar(dist, n * args.steps, "sum") / t_max
-    alg_bytes = sum(i["n"] * (16 + 4 + 16) + 4 * i["neighbors_total"] for i in infos)
+    alg_bytes = sum(i["n"] * (16 + 4 + 96 + 16 + 16) + 4 * i["neighbors_total"] for i in infos)
     peak, peak_kind = measured_peaks()
     f_mean = float(force_ms.mean())
     achieved = alg_bytes / (f_mean * 1e-3) / 1e9

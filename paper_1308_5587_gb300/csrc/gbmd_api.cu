@@ -254,26 +254,46 @@ std::vector<KernelCall> rebuild_calls(const Group* g) {
           nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi, g->ntbk > 0)};
 }
 
-KernelCall step_force_call(const Group* g, int ev, int force_all) {
-  return force_call(g->precision, g->multi, ev, g->tpp, g->fblock, g->d_desc, g->d_tf, g->ntf,
-                    g->d_ctl, force_all);
+// forces at the current positions, outside the step (autotuning, readouts)
+KernelCall plain_force_call(const Group* g) {
+  return force_call(g->precision, g->multi, MODE_FORCE, g->tpp, g->fblock, g->d_desc, g->d_tf,
+                    g->ntf, g->d_ctl, StepArgs{});
 }
 
 // energy/virial launch of the global-list systems: the step's threads per particle
 // (so the FP32 forces it writes are bitwise the step's), EV_TILE_P particles per block
-KernelCall ev_force_call(const Group* g, const SysDev* desc, int force_all) {
-  return force_call(g->precision, g->multi, 1, g->tpp, EV_TILE_P * g->tpp, desc, g->d_te, g->nte,
-                    g->d_ctl, force_all);
+KernelCall ev_force_call(const Group* g, const SysDev* desc) {
+  return force_call(g->precision, g->multi, MODE_EV, g->tpp, EV_TILE_P * g->tpp, desc, g->d_te,
+                    g->nte, g->d_ctl, StepArgs{});
 }
 
-// the force launches of a step (ev = 0) or of a readout (ev = 1): global-list
-// systems, then staged ones
-std::vector<KernelCall> force_calls(const Group* g, int ev, int force_all) {
+// readout force launches (ev = 0 forces, 1 also energy/virial): global-list systems,
+// then staged ones
+std::vector<KernelCall> force_calls(const Group* g, int ev) {
   std::vector<KernelCall> v;
-  if (g->ntf > 0) v.push_back(ev ? ev_force_call(g, g->d_desc, force_all) : step_force_call(g, 0, force_all));
+  if (g->ntf > 0) v.push_back(ev ? ev_force_call(g, g->d_desc) : plain_force_call(g));
   if (g->ntb > 0)
-    v.push_back(force_staged_call(g->multi, ev, g->d_desc, g->d_tb, g->ntb, g->d_ctl, force_all,
-                                  g->nte, g->window_cap));
+    v.push_back(force_staged_call(g->multi, ev ? MODE_EV : MODE_FORCE, g->d_desc, g->d_tb, g->ntb,
+                                  g->d_ctl, g->nte, g->window_cap, StepArgs{}));
+  return v;
+}
+
+// the step kernels: force + integrate of every member, global-list systems then
+// staged ones; the last of all their blocks makes the step's decisions and sets
+// `cond` (when use_cond) for the rebuild that follows
+std::vector<KernelCall> step_calls(const Group* g, cudaGraphConditionalHandle cond, int use_cond) {
+  StepArgs sa;
+  sa.nsys = (int)live(g).size();
+  sa.total_blocks = g->ntf + g->ntb;
+  sa.cond = cond;
+  sa.use_cond = use_cond;
+  std::vector<KernelCall> v;
+  if (g->ntf > 0)
+    v.push_back(force_call(g->precision, g->multi, MODE_STEP, g->tpp, g->fblock, g->d_desc, g->d_tf,
+                           g->ntf, g->d_ctl, sa));
+  if (g->ntb > 0)
+    v.push_back(force_staged_call(g->multi, MODE_STEP, g->d_desc, g->d_tb, g->ntb, g->d_ctl, g->nte,
+                                  g->window_cap, sa));
   return v;
 }
 
@@ -303,16 +323,33 @@ int build_graph(Group* g, int nsteps, cudaGraphExec_t* exec) {
     cudaGraphConditionalHandle h;
     cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "conditional handle: %s", cudaGetErrorString(e)); break; }
-    cudaGraphNode_t n6, nc, n5;
-    rc = add_kernel(graph, prev ? &prev : nullptr,
-                    integrate_call(g->precision, g->d_desc, g->d_tp, g->ntp, g->d_ctl, nsys, h, 1), &n6);
+    // force + integrate (event nodes around them when asked), then IF(rebuild){lists}
+    cudaGraphNode_t before = prev;
+    if (events) {
+      e = cudaGraphAddEventRecordNode(&g->node_ev_begin, graph, before ? &before : nullptr, before ? 1 : 0,
+                                      g->ev_begin);
+      if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "event node: %s", cudaGetErrorString(e)); break; }
+      before = g->node_ev_begin;
+    }
+    for (const KernelCall& k : step_calls(g, h, 1)) {
+      cudaGraphNode_t n5;
+      rc = add_kernel(graph, before ? &before : nullptr, k, &n5);
+      if (rc) break;
+      before = n5;
+    }
     if (rc) break;
+    if (events) {
+      e = cudaGraphAddEventRecordNode(&g->node_ev_end, graph, &before, 1, g->ev_end);
+      if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "event node: %s", cudaGetErrorString(e)); break; }
+      before = g->node_ev_end;
+    }
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeIf;
     cp.conditional.size = 1;
-    e = cudaGraphAddNode(&nc, graph, &n6, nullptr, 1, &cp);
+    cudaGraphNode_t nc;
+    e = cudaGraphAddNode(&nc, graph, &before, nullptr, 1, &cp);
     if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "conditional node: %s", cudaGetErrorString(e)); break; }
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaGraphNode_t bprev = nullptr;
@@ -323,24 +360,7 @@ int build_graph(Group* g, int nsteps, cudaGraphExec_t* exec) {
       bprev = bn;
     }
     if (rc) break;
-    cudaGraphNode_t before = nc;
-    if (events) {
-      e = cudaGraphAddEventRecordNode(&g->node_ev_begin, graph, &nc, 1, g->ev_begin);
-      if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "event node: %s", cudaGetErrorString(e)); break; }
-      before = g->node_ev_begin;
-    }
-    for (const KernelCall& k : force_calls(g, 0, 0)) {
-      rc = add_kernel(graph, &before, k, &n5);
-      if (rc) break;
-      before = n5;
-    }
-    if (rc) break;
-    prev = before;
-    if (events) {
-      e = cudaGraphAddEventRecordNode(&g->node_ev_end, graph, &before, 1, g->ev_end);
-      if (e != cudaSuccess) { rc = fail(GBMD_ERR_CUDA, "event node: %s", cudaGetErrorString(e)); break; }
-      prev = g->node_ev_end;
-    }
+    prev = nc;
   }
   if (rc == GBMD_OK) {
     cudaError_t e = cudaGraphInstantiate(exec, graph, 0);
@@ -370,14 +390,12 @@ int enqueue_steps(Group* g, long long n) {
     for (long long k = 0; k < n % STEPS_PER_GRAPH; ++k) CK(cudaGraphLaunch(g->exec_one, g->stream));
     return GBMD_OK;
   }
-  const int nsys = (int)live(g).size();
   for (long long k = 0; k < n; ++k) {
-    CK(launch(integrate_call(g->precision, g->d_desc, g->d_tp, g->ntp, g->d_ctl, nsys, 0, 0), g->stream));
-    for (const KernelCall& c : rebuild_calls(g)) CK(launch(c, g->stream));
     const bool events = n == 1 && g->ev_begin && g->ev_end;
     if (events) CK(cudaEventRecord(g->ev_begin, g->stream));
-    for (const KernelCall& c : force_calls(g, 0, 0)) CK(launch(c, g->stream));
+    for (const KernelCall& c : step_calls(g, 0, 0)) CK(launch(c, g->stream));
     if (events) CK(cudaEventRecord(g->ev_end, g->stream));
+    for (const KernelCall& c : rebuild_calls(g)) CK(launch(c, g->stream));
   }
   return GBMD_OK;
 }
@@ -401,7 +419,7 @@ int rebuild_and_force(gbmd_system* s, int ev) {
   Group* g = s->own;
   RET(sync_layout(g));
   for (const KernelCall& c : rebuild_calls(g)) CK(launch(c, g->stream));
-  for (const KernelCall& c : force_calls(g, ev, 1)) CK(launch(c, g->stream));
+  for (const KernelCall& c : force_calls(g, ev)) CK(launch(c, g->stream));
   return GBMD_OK;
 }
 
@@ -561,8 +579,8 @@ size_t footprint_of(const gbmd_desc* d, const Geometry& g) {
   size_t b = 0;
   b += n * (8 * 3 * 2);          // x, v
   b += n * 4 * 3 + n * 4 * 3;    // img, rtag/tag/type
-  b += n * 16 * 2;               // q, q_build
-  b += n * 32;                   // p64
+  b += n * 16 * 3;               // q (two step-parity buffers), q_build
+  if (d->precision == GBMD_FP64) b += n * 32 * 2;   // p64 (two buffers)
   b += n * (d->precision == GBMD_FP64 ? 32 : 16);   // force
   b += n * 4 + round_up(n, 32) * 4 * (size_t)g.cap;  // nn, nl (ELL4)
   b += n * 4 * 4 + (size_t)(g.ncells + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;  // cells
@@ -719,7 +737,10 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   const size_t N = (size_t)n;
   A((void**)&h.x, N * 24); A((void**)&h.v, N * 24); A((void**)&h.img, N * 12);
   A((void**)&h.type, N * 4); A((void**)&h.tag, N * 4); A((void**)&h.rtag, N * 4);
-  A((void**)&h.q, N * 16); A((void**)&h.q_build, N * 16); A((void**)&h.p64, N * 32);
+  A((void**)&h.q, N * 16); A((void**)&h.q1, N * 16); A((void**)&h.q_build, N * 16);
+  if (d->precision == GBMD_FP64) {
+    A((void**)&h.p64, N * 32); A((void**)&h.p64b, N * 32);
+  }
   if (d->precision == GBMD_FP64) A((void**)&h.f64, N * 32); else A((void**)&h.f32, N * 16);
   A((void**)&h.nn, N * 4); A((void**)&h.nl, round_up(N, 32) * 4 * (size_t)geo.cap);
   A((void**)&h.key, N * 4); A((void**)&h.members, N * 4); A((void**)&h.members_tmp, N * 4);
@@ -830,7 +851,7 @@ int thermo_impl(gbmd_system* s, double out[8]) {
   Group* g = s->own;
   RET(sync_layout(g));
   cudaStream_t st = cur_stream(s);
-  for (const KernelCall& c : force_calls(g, 1, 1)) CK(launch(c, st));
+  for (const KernelCall& c : force_calls(g, 1)) CK(launch(c, st));
   CK(launch(thermo_call(g->d_desc, g->d_ts, g->nts, g->d_ctl), st));
   CK(cudaMemcpyAsync(out, s->d_thermo, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -844,6 +865,10 @@ int export_impl(gbmd_system* s, double* pos, double* vel, int32_t* image, double
   cudaStream_t st = cur_stream(s);
   const size_t N = (size_t)s->h.n;
   if ((pp_u || pp_w) && !s->d_ppw) return fail(GBMD_ERR_STATE, "per-particle arrays not allocated");
+  // forces and full-step velocities need F at the current positions: the step kernel
+  // does not store its force, so evaluate it here
+  if (vel || force)
+    for (const KernelCall& c : force_calls(g, 0)) CK(launch(c, st));
   CK(launch(export_call(g->d_desc, g->d_tp, g->ntp, pos ? s->d_pos : nullptr,
                         vel ? s->d_vel : nullptr, image ? s->d_img : nullptr,
                         force ? s->d_frc : nullptr, pp_u ? s->d_ppu : nullptr,
@@ -867,10 +892,10 @@ int time_force(Group* g, float* ms) {
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
-  for (int k = 0; k < 2; ++k) CK(launch(step_force_call(g, 0, 1), g->stream));
+  for (int k = 0; k < 2; ++k) CK(launch(plain_force_call(g), g->stream));
   CK(cudaEventRecord(a, g->stream));
   const int reps = 5;
-  for (int k = 0; k < reps; ++k) CK(launch(step_force_call(g, 0, 1), g->stream));
+  for (int k = 0; k < reps; ++k) CK(launch(plain_force_call(g), g->stream));
   CK(cudaEventRecord(b, g->stream));
   CK(cudaEventSynchronize(b));
   float t = 0;
@@ -1538,10 +1563,10 @@ extern "C" int gbmd_get_thermo_noalloc(gbmd_system* s, gbmd_thermo* out) {
   d.tile_count_f = g->nte + g->ntb;   // the system alone: one of the two is zero
   d.partials = addr.partials;
   CK(cudaMemcpyAsync(addr.desc, &d, sizeof(SysDev), cudaMemcpyHostToDevice, st));
-  if (g->ntf > 0) CK(launch(ev_force_call(g, addr.desc, 1), st));
+  if (g->ntf > 0) CK(launch(ev_force_call(g, addr.desc), st));
   if (g->ntb > 0)
-    CK(launch(force_staged_call(g->multi, 1, addr.desc, g->d_tb, g->ntb, g->d_ctl, 1, 0,
-                                g->window_cap), st));
+    CK(launch(force_staged_call(g->multi, MODE_EV, addr.desc, g->d_tb, g->ntb, g->d_ctl, 0,
+                                g->window_cap, StepArgs{}), st));
   CK(launch(thermo_call(addr.desc, g->d_ts, g->nts, g->d_ctl), st));
   double t[8];
   CK(cudaMemcpyAsync(t, s->d_thermo, sizeof(t), cudaMemcpyDeviceToHost, st));

@@ -117,8 +117,11 @@ struct SysDev {
   // particle arrays
   double *x, *v;
   int *img, *type, *tag, *rtag;
-  int4 *q, *q_build;
-  double4_32a *p64;
+  // position shadows, double-buffered by step parity (q, p64: even steps; q1, p64b:
+  // odd steps): the step kernel gathers from one and writes the next step's to the
+  // other.  p64 only in FP64 mode.
+  int4 *q, *q1, *q_build;
+  double4_32a *p64, *p64b;
   float4 *f32;
   double4_32a *f64;
   int *nn, *nl;
@@ -139,7 +142,7 @@ struct SysDev {
 
 // group-level control block (one per single system or batch)
 struct GroupCtl {
-  unsigned int blocks_done;  // last-block counter of the integrate kernel
+  unsigned int blocks_done;  // last-block counter of the step kernel
   int any_rebuild;
   unsigned long long launches;
 };
@@ -147,6 +150,20 @@ struct GroupCtl {
 struct Tile { int sys, first, count, pad; };
 
 // ---- device helpers -------------------------------------------------------
+
+// a system's step counter (written by the last block of each step)
+__device__ __forceinline__ long long step_of(const Flags* f) {
+  long long r;
+  asm volatile("ld.volatile.global.s64 %0, [%1];" : "=l"(r) : "l"(&f->step));
+  return r;
+}
+// the shadow of the positions at step `step` (and the buffer for step + 1)
+__device__ __forceinline__ int4* q_at(const SysDev& s, long long step) {
+  return (step & 1) ? s.q1 : s.q;
+}
+__device__ __forceinline__ double4_32a* p64_at(const SysDev& s, long long step) {
+  return (step & 1) ? s.p64b : s.p64;
+}
 
 __device__ __forceinline__ void count_launch(const SysDev& s) {
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&s.flags->launches, 1ull);

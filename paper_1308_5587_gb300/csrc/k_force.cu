@@ -27,6 +27,7 @@
 // FP64: positions come from the double4 shadow p64; the minimum image is one
 // conditional correction by L (|d| < L for wrapped coordinates); all arithmetic FP64.
 #include "launch.cuh"
+#include "step_core.cuh"
 
 namespace gbmd {
 
@@ -127,18 +128,26 @@ __device__ __forceinline__ void pair2(const int4& qi, const int4& qa, const int4
   }
 }
 
-template <int PREC, int TPP, int MT, bool EV>
+// MODE_FORCE: forces at the current positions (readouts); MODE_EV: also the
+// energy / virial / v.v partial sums; MODE_STEP: the step kernel -- forces, then each
+// particle's velocity Verlet update into the next shadow buffer (step_core.cuh), then
+// the end-of-step decisions by the last of `total_blocks` blocks.  A system that is
+// frozen (device error) or at its step limit is skipped in step mode.
+template <int PREC, int TPP, int MT, int MODE>
 __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
                                                const Tile* __restrict__ tiles, GroupCtl* ctl,
-                                               int force_all) {
+                                               int nsys, int total_blocks,
+                                               cudaGraphConditionalHandle cond, int use_cond) {
+  constexpr bool EV = MODE == MODE_EV, STEP = MODE == MODE_STEP;
   const Tile t = tiles[blockIdx.x];
   const SysDev& s = sysv[t.sys];
   if (threadIdx.x == 0 && t.first == 0) atomicAdd(&s.flags->launches, 1ull);
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
-  if (!force_all) {
-    const FlagWords fw = load_flag_words(s.flags);
-    if (!fw.active || fw.error) return;   // uniform over the block
-  }
+  const FlagWords fw = load_flag_words(s.flags);
+  const longlong2 sl = load_flag_pair(&s.flags->step);   // (step, step_limit)
+  const bool active = !STEP || (fw.error == 0 && (sl.y < 0 || sl.x < sl.y));   // uniform
+  const long long step = sl.x;
+  bool need = false, bad = false;
   const int nt = s.ntypes;
   constexpr bool SMEM_TAB = PREC == GBMD_MIXED ? MT == 2 : MT != 0;
   __shared__ PairF tabf[SMEM_TAB ? MAXT2 : 1];
@@ -152,6 +161,7 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
   const int g = threadIdx.x / TPP, h = threadIdx.x % TPP;
   const bool valid = g < t.count;
   const int i = t.first + (valid ? g : 0);
+  if (active) {
   const int n = valid ? s.nn[i] : 0;
   const int groups = (n + 3) >> 2;
   const int4* __restrict__ nl4 = reinterpret_cast<const int4*>(s.nl) + i;
@@ -161,7 +171,8 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
   int4 jn = h < cap_groups ? __ldg(nl4 + (size_t)h * stride) : make_int4(i, i, i, i);
 
   if (PREC == GBMD_MIXED) {
-    const int4 qi = s.q[i];
+    const int4* __restrict__ qv = q_at(s, step);
+    const int4 qi = qv[i];
     const float2 sc0 = make_float2(s.fscale[0], s.fscale[0]);
     const float2 sc1 = make_float2(s.fscale[1], s.fscale[1]);
     const float2 sc2 = make_float2(s.fscale[2], s.fscale[2]);
@@ -175,7 +186,6 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
       if (MT == 1) return tj ? r1 : r0;
       return tabf[qi.w * nt + tj];
     };
-    const int4* __restrict__ qv = s.q;
     float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx, e = fx;
     float2 w[6] = {fx, fx, fx, fx, fx, fx};
     for (int gg = h; gg < groups; gg += TPP) {
@@ -200,11 +210,18 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
       E = group_sum<TPP>(e.x + e.y);
       for (int c = 0; c < 6; ++c) W[c] = group_sum<TPP>(w[c].x + w[c].y);
     }
-    if (valid && h == 0) s.f32[i] = make_float4(Fx, Fy, Fz, EV ? E : 0.f);
+    if (STEP) {   // the step needs no stored force: each lane-0 integrates its particle
+      if (valid && h == 0) {
+        const double f[3] = {widen_f32(Fx, bad), widen_f32(Fy, bad), widen_f32(Fz, bad)};
+        integrate_one<PREC>(s, i, qi.w, f, fw.v_full, q_at(s, step + 1), nullptr, need, bad);
+      }
+    } else if (valid && h == 0) {
+      s.f32[i] = make_float4(Fx, Fy, Fz, EV ? E : 0.f);
+    }
     if (EV) {
       double vals[NPART] = {valid ? (double)E : 0.0};
       for (int c = 0; c < 6; ++c) vals[c + 1] = valid ? (double)W[c] : 0.0;
-      vals[7] = valid ? vsq(s, i, Fx, Fy, Fz, ((const volatile Flags*)s.flags)->v_full) : 0.0;
+      vals[7] = valid ? vsq(s, i, Fx, Fy, Fz, fw.v_full) : 0.0;
       if (valid && h == 0 && s.pp_u) {
         s.pp_u[i] = vals[0];
         for (int c = 0; c < 6; ++c) s.pp_w[6 * (size_t)i + c] = vals[c + 1];
@@ -212,13 +229,13 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
       reduce_partials<TPP, 512>(vals, s.partials + 8 * (size_t)blockIdx.x);
     }
   } else {
-    const double4_32a pi = s.p64[i];
+    const double4_32a* __restrict__ pv = p64_at(s, step);
+    const double4_32a pi = pv[i];
     const int ti = (int)__double_as_longlong(pi.w);
     const double L0 = s.L[0], L1 = s.L[1], L2 = s.L[2];
     const int h0 = __double2hiint(s.halfL[0]), h1 = __double2hiint(s.halfL[1]),
               h2 = __double2hiint(s.halfL[2]);
     const PairD p0 = s.pd[0];
-    const double4_32a* __restrict__ pv = s.p64;
     double fx = 0, fy = 0, fz = 0, e = 0;
     double w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     for (int gg = h; gg < groups; gg += TPP) {
@@ -270,11 +287,19 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
       w0 = group_sum<TPP>(w0); w1 = group_sum<TPP>(w1); w2 = group_sum<TPP>(w2);
       w3 = group_sum<TPP>(w3); w4 = group_sum<TPP>(w4); w5 = group_sum<TPP>(w5);
     }
-    if (valid && h == 0) s.f64[i] = make_double4_32a(fx, fy, fz, EV ? e : 0.0);
+    if (STEP) {
+      if (valid && h == 0) {
+        const double f[3] = {fx, fy, fz};
+        bad |= !isfinite(fx) || !isfinite(fy) || !isfinite(fz);
+        integrate_one<PREC>(s, i, ti, f, fw.v_full, q_at(s, step + 1), p64_at(s, step + 1), need, bad);
+      }
+    } else if (valid && h == 0) {
+      s.f64[i] = make_double4_32a(fx, fy, fz, EV ? e : 0.0);
+    }
     if (EV) {
       double vals[NPART] = {valid ? e : 0.0,  valid ? w0 : 0.0, valid ? w1 : 0.0, valid ? w2 : 0.0,
                             valid ? w3 : 0.0, valid ? w4 : 0.0, valid ? w5 : 0.0,
-                            valid ? vsq(s, i, fx, fy, fz, ((const volatile Flags*)s.flags)->v_full) : 0.0};
+                            valid ? vsq(s, i, fx, fy, fz, fw.v_full) : 0.0};
       if (valid && h == 0 && s.pp_u) {
         s.pp_u[i] = vals[0];
         for (int c = 0; c < 6; ++c) s.pp_w[6 * (size_t)i + c] = vals[c + 1];
@@ -282,6 +307,8 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
       reduce_partials<TPP, 512>(vals, s.partials + 8 * (size_t)blockIdx.x);
     }
   }
+  }   // active
+  if (STEP) step_tail(s, sysv, ctl, nsys, total_blocks, cond, use_cond, need, bad);
 }
 
 // ---- staged path: one kernel block per aligned 2x2x2 block of cells ----------------
@@ -291,25 +318,30 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
 // Its particles' lists hold 16-bit window-local indices (ELL8: one int4 = 8 entries
 // of one member), so every neighbour position comes from shared memory and the
 // index stream is half as long.  One thread per particle.
-template <int MT, bool EV>
+template <int MT, int MODE>
 __global__ void __launch_bounds__(STAGED_BLOCK) k_force_staged(const SysDev* __restrict__ sysv,
                                                                const Tile* __restrict__ tiles,
-                                                               GroupCtl* ctl, int force_all,
-                                                               int part_base) {
+                                                               GroupCtl* ctl, int part_base,
+                                                               int nsys, int total_blocks,
+                                                               cudaGraphConditionalHandle cond,
+                                                               int use_cond) {
+  constexpr bool EV = MODE == MODE_EV, STEP = MODE == MODE_STEP;
   extern __shared__ int wsm[];   // window as three int arrays: x, y, z | type
   const Tile t = tiles[blockIdx.x];
   const SysDev& s = sysv[t.sys];
   if (threadIdx.x == 0 && t.first == 0) atomicAdd(&s.flags->launches, 1ull);
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
-  {
-    const FlagWords fw = load_flag_words(s.flags);
-    if (fw.error) return;                   // e.g. a window too large: nothing is valid
-    if (!force_all && !fw.active) return;   // uniform over the block
-  }
+  const FlagWords fw = load_flag_words(s.flags);
+  const longlong2 sl = load_flag_pair(&s.flags->step);   // (step, step_limit)
+  const long long step = sl.x;
   const int b = t.first;
   const int4 info = s.blk_info[b];          // (first member, particles, window total, 0)
-  if (info.z > s.window_cap) return;        // never index past the staged window
-  const int4* __restrict__ qv = s.q;
+  // an error (e.g. a window too large) leaves nothing valid, and a window is never
+  // indexed past its capacity; step mode also skips a system at its step limit
+  const bool run = fw.error == 0 && info.z <= s.window_cap && (!STEP || sl.y < 0 || sl.x < sl.y);
+  bool need = false, bad = false;
+  if (run) {
+  const int4* __restrict__ qv = q_at(s, step);
   const int* __restrict__ members = s.members;
   // stage the window: the 64 (start, offset) pairs first, then every thread copies
   // window entries tid, tid + 256, ... (independent loads, several in flight)
@@ -356,7 +388,7 @@ __global__ void __launch_bounds__(STAGED_BLOCK) k_force_staged(const SysDev* __r
   const size_t stride = (size_t)s.nl_stride;
   const int4* __restrict__ nl8 = reinterpret_cast<const int4*>(s.nl);
   double acc[NPART] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const int vfull = EV ? ((const volatile Flags*)s.flags)->v_full : 1;
+  const int vfull = fw.v_full;
   for (int pidx = threadIdx.x; pidx < info.y; pidx += STAGED_BLOCK) {
     const int m = info.x + pidx;
     const int i = members[m];
@@ -394,7 +426,12 @@ __global__ void __launch_bounds__(STAGED_BLOCK) k_force_staged(const SysDev* __r
       }
     }
     const float Fx = fx.x + fx.y, Fy = fy.x + fy.y, Fz = fz.x + fz.y;
-    s.f32[i] = make_float4(Fx, Fy, Fz, EV ? e.x + e.y : 0.f);
+    if (STEP) {
+      const double f[3] = {widen_f32(Fx, bad), widen_f32(Fy, bad), widen_f32(Fz, bad)};
+      integrate_one<GBMD_MIXED>(s, i, qi.w, f, vfull, q_at(s, step + 1), nullptr, need, bad);
+    } else {
+      s.f32[i] = make_float4(Fx, Fy, Fz, EV ? e.x + e.y : 0.f);
+    }
     if (EV) {
       double v[NPART] = {(double)(e.x + e.y)};
       for (int c = 0; c < 6; ++c) v[c + 1] = (double)(w[c].x + w[c].y);
@@ -416,55 +453,70 @@ __global__ void __launch_bounds__(STAGED_BLOCK) k_force_staged(const SysDev* __r
       s.partials[8 * (size_t)(part_base + blockIdx.x) + threadIdx.x] = a;
     }
   }
+  }   // run
+  if (STEP) step_tail(s, sysv, ctl, nsys, total_blocks, cond, use_cond, need, bad);
 }
 
 bool tpp_supported(int tpp) { return tpp == 1 || tpp == 2 || tpp == 4; }
 
-template <int PREC, int TPP>
-static void* pick3(int mt, int ev) {
-  if constexpr (PREC == GBMD_FP64) {
-    mt = mt ? 2 : 0;   // one FP64 table mode
-  } else {
-    if (mt == 1) return ev ? (void*)k_force<PREC, TPP, 1, true> : (void*)k_force<PREC, TPP, 1, false>;
+template <int PREC, int TPP, int MT>
+static void* pick4(int mode) {
+  switch (mode) {
+    case MODE_EV: return (void*)k_force<PREC, TPP, MT, MODE_EV>;
+    case MODE_STEP: return (void*)k_force<PREC, TPP, MT, MODE_STEP>;
+    default: return (void*)k_force<PREC, TPP, MT, MODE_FORCE>;
   }
-  if (mt == 2) return ev ? (void*)k_force<PREC, TPP, 2, true> : (void*)k_force<PREC, TPP, 2, false>;
-  return ev ? (void*)k_force<PREC, TPP, 0, true> : (void*)k_force<PREC, TPP, 0, false>;
+}
+
+template <int PREC, int TPP>
+static void* pick3(int mt, int mode) {
+  if constexpr (PREC == GBMD_FP64) {
+    return mt ? pick4<PREC, TPP, 2>(mode) : pick4<PREC, TPP, 0>(mode);   // one FP64 table mode
+  } else {
+    if (mt == 1) return pick4<PREC, TPP, 1>(mode);
+    if (mt == 2) return pick4<PREC, TPP, 2>(mode);
+    return pick4<PREC, TPP, 0>(mode);
+  }
 }
 
 template <int PREC>
-static void* pick2(int tpp, int mt, int ev) {
+static void* pick2(int tpp, int mt, int mode) {
   switch (tpp) {
-    case 1: return pick3<PREC, 1>(mt, ev);
-    case 2: return pick3<PREC, 2>(mt, ev);
-    default: return pick3<PREC, 4>(mt, ev);
+    case 1: return pick3<PREC, 1>(mt, mode);
+    case 2: return pick3<PREC, 2>(mt, mode);
+    default: return pick3<PREC, 4>(mt, mode);
   }
 }
 
 // multi: 0 = one type, 1 = at most two types, 2 = up to MAXT types
-KernelCall force_call(int prec, int multi, int ev, int tpp, int block, const SysDev* d,
-                      const Tile* tiles_f, int ntiles, GroupCtl* ctl, int force_all) {
+KernelCall force_call(int prec, int multi, int mode, int tpp, int block, const SysDev* d,
+                      const Tile* tiles_f, int ntiles, GroupCtl* ctl, const StepArgs& sa) {
   // the FP64 kernel is FP64-pipe bound: its table stays in shared memory
-  void* f = prec == GBMD_FP64 ? pick2<GBMD_FP64>(tpp, multi, ev) : pick2<GBMD_MIXED>(tpp, multi, ev);
+  void* f = prec == GBMD_FP64 ? pick2<GBMD_FP64>(tpp, multi, mode) : pick2<GBMD_MIXED>(tpp, multi, mode);
   KernelCall k = make_call(f, ntiles, block, 0);
-  put(k, d); put(k, tiles_f); put(k, ctl); put(k, force_all);
+  put(k, d); put(k, tiles_f); put(k, ctl); put(k, sa.nsys); put(k, sa.total_blocks);
+  put(k, sa.cond); put(k, sa.use_cond);
   return k;
 }
 
-KernelCall force_staged_call(int multi, int ev, const SysDev* d, const Tile* tiles_s, int ntiles,
-                             GroupCtl* ctl, int force_all, int part_base, int window_cap) {
-  void* const fs[3][2] = {{(void*)k_force_staged<0, false>, (void*)k_force_staged<0, true>},
-                          {(void*)k_force_staged<1, false>, (void*)k_force_staged<1, true>},
-                          {(void*)k_force_staged<2, false>, (void*)k_force_staged<2, true>}};
+KernelCall force_staged_call(int multi, int mode, const SysDev* d, const Tile* tiles_s, int ntiles,
+                             GroupCtl* ctl, int part_base, int window_cap, const StepArgs& sa) {
+  void* const fs[3][3] = {
+      {(void*)k_force_staged<0, MODE_FORCE>, (void*)k_force_staged<0, MODE_EV>, (void*)k_force_staged<0, MODE_STEP>},
+      {(void*)k_force_staged<1, MODE_FORCE>, (void*)k_force_staged<1, MODE_EV>, (void*)k_force_staged<1, MODE_STEP>},
+      {(void*)k_force_staged<2, MODE_FORCE>, (void*)k_force_staged<2, MODE_EV>, (void*)k_force_staged<2, MODE_STEP>}};
   const int mt = multi < 0 ? 0 : multi > 2 ? 2 : multi;
-  void* f = fs[mt][ev ? 1 : 0];
+  const int md = mode < 0 ? 0 : mode > 2 ? 2 : mode;
+  void* f = fs[mt][md];
   const size_t smem = (size_t)window_cap * 3 * sizeof(int);
-  static bool attr_set[3][2] = {};
-  if (!attr_set[mt][ev ? 1 : 0]) {   // dynamic shared memory above the 48 KB default
+  static bool attr_set[3][3] = {};
+  if (!attr_set[mt][md]) {   // dynamic shared memory above the 48 KB default
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr_set[mt][ev ? 1 : 0] = true;
+    attr_set[mt][md] = true;
   }
   KernelCall k = make_call(f, ntiles, STAGED_BLOCK, smem);
-  put(k, d); put(k, tiles_s); put(k, ctl); put(k, force_all); put(k, part_base);
+  put(k, d); put(k, tiles_s); put(k, ctl); put(k, part_base); put(k, sa.nsys);
+  put(k, sa.total_blocks); put(k, sa.cond); put(k, sa.use_cond);
   return k;
 }
 

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(TILE_P) k_bin(const SysDev* __restrict__ sysv,
   count(s, t, ctl);
   if (!rebuilding(s) || threadIdx.x >= t.count) return;
   const int i = t.first + threadIdx.x;
-  const int4 q = s.q[i];
+  const int4 q = q_at(s, step_of(s.flags))[i];
   const int cx = cell_of_fixed(q.x, s.nc[0]);
   const int cy = cell_of_fixed(q.y, s.nc[1]);
   const int cz = cell_of_fixed(q.z, s.nc[2]);
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(TILE_P) k_permute(const SysDev* __restrict__ s
   }
   s.type_alt[k] = s.type[o];
   s.tag_alt[k] = s.tag[o];
-  s.q_alt[k] = s.q[o];
+  s.q_alt[k] = q_at(s, step_of(s.flags))[o];
 }
 
 __global__ void __launch_bounds__(TILE_P) k_copyback(const SysDev* __restrict__ sysv,
@@ -193,10 +193,12 @@ __global__ void __launch_bounds__(TILE_P) k_copyback(const SysDev* __restrict__ 
   const int tg = s.tag_alt[k];
   s.tag[k] = tg;
   s.rtag[tg] = k;
-  s.q[k] = s.q_alt[k];
+  const long long step = step_of(s.flags);
+  q_at(s, step)[k] = s.q_alt[k];
   s.members[k] = k;
   s.rmember[k] = k;
-  if (s.precision == GBMD_FP64) s.p64[k] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
+  if (s.precision == GBMD_FP64)
+    p64_at(s, step)[k] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
 }
 
 // ---- staged force tiles: the window of every aligned 2x2x2 block of cells ----
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   const int b = s.cell_start[r], e = s.cell_start[r + 1];
   const int cap = s.cap;
   const int* __restrict__ members = s.members;
-  const int4* __restrict__ qv = s.q;
+  const int4* __restrict__ qv = q_at(s, step_of(s.flags));
   const bool two = !MULTI || nt <= 2;
   __syncwarp();
 

@@ -1,185 +1,18 @@
-// k_step.cu -- integrate (velocity Verlet, fused leapfrog form), thermo reduction,
-// and the import/export kernels of the C ABI.
+// k_step.cu -- thermo reduction and the import/export kernels of the C ABI.
 //
 // Velocity Verlet (NVE; Listing 1's mode_standard(dt) + run(n), NVE per Section 3.1):
 //   v <- v + dt/(2m) F(t);  x <- x + dt v;  wrap;  F(t+dt);  v <- v + dt/(2m) F(t+dt).
-// The closing half kick of step n and the opening half kick of step n+1 are applied
-// back to back at the start of step n+1 by one kernel (k_integrate), so the stored
-// velocity lags half a kick behind the full-step velocity between steps
-// (Flags::v_full says when it does not, i.e. right after create / set_state).
-// Positions are stored in FP64 in units of L/2^32 per axis (xq = x * 2^32 / L), so
-// the drift is one FMA and the 32-bit fixed-point shadow used by the neighbour
-// list and the mixed-precision force is one conversion.
+// The step kernel (k_force in step mode, step_core.cuh) computes F(x^n) and then
+// applies the closing half kick of step n-1 and the opening half kick of step n back
+// to back, so the stored velocity lags half a kick behind the full-step velocity
+// between steps (Flags::v_full says when it does not, i.e. right after create /
+// set_state); readouts add h F(x^n) with the force at the current positions.
+// Positions are stored in FP64 in units of L/2^32 per axis (xq = x * 2^32 / L).
 #include <cstring>
 
 #include "launch.cuh"
 
 namespace gbmd {
-
-// ---------------------------------------------------------------------------
-// K6: kicks + drift + wrap + fixed-point shadow + displacement check, then the
-// last block of the grid makes the per-step decisions for every system.
-// FP64 runs at about 1/80 of the FP32 FMA rate on this part (measured: 1.6 against
-// 128 FMAs per SM per clock), so the kernel keeps the FP64
-// pipe to the six FMAs of the kicks and drifts plus one add per axis: the FP32
-// force is widened to FP64 with integer operations (IEEE-754 field by field), and
-// rint of the position uses the 1.5 * 2^52 rounding constant instead of a
-// conversion instruction.
-// ---------------------------------------------------------------------------
-
-// float -> double, exactly, on the integer pipe.  Zero and subnormal inputs (a
-// force below 1.2e-38) give zero; inf / NaN set `bad`.
-__device__ __forceinline__ double widen_f32(float f, bool& bad) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ex = (u >> 23) & 0xffu;
-  bad |= ex == 0xffu;
-  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned long long mag = ((unsigned long long)(ex + 896u) << 52) |   // 1023 - 127
-                                 ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)(sign | (ex ? mag : 0ull)));
-}
-
-// rint(x) (ties to even) as an integer for |x| < 2^51: x + 1.5 * 2^52 lies in
-// [2^52, 2^53), where the spacing of doubles is 1, so the sum is rounded to an
-// integer and its bit pattern minus the constant's is that integer
-__device__ __forceinline__ long long rint_ll(double x) {
-  const double m = x + 6755399441055744.0;
-  return __double_as_longlong(m) - 0x4338000000000000LL;
-}
-template <int PREC>
-__global__ void __launch_bounds__(TILE_P) k_integrate(const SysDev* __restrict__ sysv,
-                                                      const Tile* __restrict__ tiles,
-                                                      GroupCtl* ctl, int nsys,
-                                                      cudaGraphConditionalHandle cond,
-                                                      int use_cond) {
-  const Tile t = tiles[blockIdx.x];
-  const SysDev& s = sysv[t.sys];
-  Flags* fl = s.flags;
-  if (threadIdx.x == 0 && t.first == 0) atomicAdd(&fl->launches, 1ull);
-  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
-  const FlagWords fw = load_flag_words(fl);
-  const longlong2 sl = load_flag_pair(&fl->step);   // (step, step_limit)
-  const bool active = fw.error == 0 && (sl.y < 0 || sl.x < sl.y);
-  const int vfull = fw.v_full;
-
-  bool need = false, bad = false;
-  const int i = t.first + threadIdx.x;
-  if (active && threadIdx.x < t.count) {
-    // descriptor fields and every load first (no store may alias them), then math
-    const int n = s.n;
-    double* __restrict__ xp = s.x;
-    double* __restrict__ vp = s.v;
-    const double kick = vfull ? s.h : s.h + s.h;   // closing + opening half kicks
-    const double dtq[3] = {s.dtq[0], s.dtq[1], s.dtq[2]};
-    const float fsc[3] = {s.fscale[0], s.fscale[1], s.fscale[2]};
-    const double Lr[3] = {s.L[0] * (1.0 / 4294967296.0), s.L[1] * (1.0 / 4294967296.0),
-                          s.L[2] * (1.0 / 4294967296.0)};
-    const float rb2 = s.rbuff_half2;
-    int* __restrict__ imgp = s.img;
-    int4* __restrict__ qp = s.q;
-    double4_32a* __restrict__ p64p = s.p64;
-    double f[3];
-    if (PREC == GBMD_FP64) {
-      const double4_32a F = s.f64[i];
-      f[0] = F.x; f[1] = F.y; f[2] = F.z;
-    } else {
-      const float4 F = __ldg(s.f32 + i);
-      f[0] = widen_f32(F.x, bad);
-      f[1] = widen_f32(F.y, bad);
-      f[2] = widen_f32(F.z, bad);
-    }
-    double v[3], xq[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      v[a] = vp[a * n + i];
-      xq[a] = xp[a * n + i];
-    }
-    const int ty = __ldg(s.type + i);
-    const int4 qb = __ldg(s.q_build + i);
-    int q[3];
-    double xr[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      v[a] = fma(kick, f[a], v[a]);
-      xq[a] = fma(dtq[a], v[a], xq[a]);
-      long long qq = rint_ll(xq[a]);
-      const long long k = (qq + 0x80000000LL) >> 32;       // floor((xq + 2^31) / 2^32)
-      if (k != 0) {
-        if (k > 1 || k < -1 || !isfinite(xq[a])) bad = true;
-        xq[a] -= (double)k * 4294967296.0;
-        qq -= k << 32;
-        imgp[a * n + i] += (int)k;
-      }
-      q[a] = (int)qq;
-      xr[a] = xq[a] * Lr[a];
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      vp[a * n + i] = v[a];
-      xp[a * n + i] = xq[a];
-    }
-    qp[i] = make_int4(q[0], q[1], q[2], ty);
-    if (PREC == GBMD_FP64) p64p[i] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
-    const float dx = (float)min_image_fixed(q[0], qb.x) * fsc[0];
-    const float dy = (float)min_image_fixed(q[1], qb.y) * fsc[1];
-    const float dz = (float)min_image_fixed(q[2], qb.z) * fsc[2];
-    need = dx * dx + dy * dy + dz * dz > rb2;
-  }
-  if (bad) atomicCAS(&fl->error, 0, (int)DEV_NONFINITE);   // rare: no block reduction
-  const int any_need = __syncthreads_or(need);
-
-  // ---- the last block to finish makes the per-step decisions ----
-  // Only thread 0 publishes: its flag update, a fence, then the arrival count
-  // (the position stores of this step need not be visible to the last block).
-  __shared__ int last;
-  if (threadIdx.x == 0) {
-    if (any_need) atomicOr(&fl->rebuild_req, 1);
-    __threadfence();
-    last = (atomicAdd(&ctl->blocks_done, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  int any = 0;
-  for (int k = threadIdx.x; k < nsys; k += blockDim.x) {
-    Flags* gf = sysv[k].flags;
-    volatile Flags* g = gf;
-    // every field the decision needs, in flight together; then the stores
-    const FlagWords w = load_flag_words(gf);
-    const longlong2 sl = load_flag_pair(&gf->step);        // (step, step_limit)
-    const longlong2 lr = load_flag_pair(&gf->last_sort);   // (last_sort, n_rebuilds)
-    const long long nsort = g->n_sorts;
-    const int sp = sysv[k].sort_period;
-    const bool act = w.error == 0 && (sl.y < 0 || sl.x < sl.y);
-    if (act) {
-      const long long st = sl.x + 1;
-      const int rb = w.rebuild_req;
-      const int srt = rb && sp > 0 && (st - lr.x >= sp);
-      g->step = st;
-      g->v_full = 0;
-      g->rebuild_req = 0;
-      g->do_rebuild = rb;
-      if (rb) g->n_rebuilds = lr.y + 1;
-      if (srt) {
-        g->last_sort = st;
-        g->n_sorts = nsort + 1;
-      }
-      g->do_sort = srt;
-      g->active = 1;
-      any |= rb;
-    } else {
-      g->active = 0;
-      g->do_rebuild = 0;
-      g->do_sort = 0;
-    }
-  }
-  any = __syncthreads_or(any);
-  if (threadIdx.x == 0) {
-    ctl->blocks_done = 0;
-    ctl->any_rebuild = any;
-    if (use_cond) cudaGraphSetConditional(cond, any ? 1u : 0u);
-  }
-}
 
 // ---------------------------------------------------------------------------
 // K7: per-system thermo.  Sums the force kernel's per-tile partials (pe, W) and
@@ -258,10 +91,17 @@ __global__ void __launch_bounds__(TILE_P) k_import(const SysDev* __restrict__ sy
   s.type[i] = ty;
   s.tag[i] = i;
   s.rtag[i] = i;
-  s.q[i] = make_int4(q[0], q[1], q[2], ty);
-  s.q_build[i] = s.q[i];
-  s.p64[i] = make_double4_32a(s.x[i] * (s.L[0] / 4294967296.0), s.x[n + i] * (s.L[1] / 4294967296.0),
-                          s.x[2 * n + i] * (s.L[2] / 4294967296.0), __longlong_as_double(ty));
+  // both shadow buffers: the step counter is set after the import
+  const int4 qn = make_int4(q[0], q[1], q[2], ty);
+  s.q[i] = qn;
+  s.q1[i] = qn;
+  s.q_build[i] = qn;
+  if (s.precision == GBMD_FP64) {   // the FP64 gather copies exist in FP64 mode only
+    const double4_32a pn = make_double4_32a(s.x[i] * (s.L[0] / 4294967296.0), s.x[n + i] * (s.L[1] / 4294967296.0),
+                                            s.x[2 * n + i] * (s.L[2] / 4294967296.0), __longlong_as_double(ty));
+    s.p64[i] = pn;
+    s.p64b[i] = pn;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -377,14 +217,6 @@ cudaError_t launch(const KernelCall& k, cudaStream_t st) {
   void* a[10];
   args_of(k, a);
   return cudaLaunchKernel(k.func, k.grid, k.block, a, k.smem, st);
-}
-
-KernelCall integrate_call(int prec, const SysDev* d, const Tile* tiles, int ntiles, GroupCtl* ctl,
-                          int nsys, cudaGraphConditionalHandle cond, int use_cond) {
-  KernelCall k = mk(prec == GBMD_FP64 ? (void*)k_integrate<GBMD_FP64> : (void*)k_integrate<GBMD_MIXED>,
-                    ntiles, TILE_P);
-  put(k, d); put(k, tiles); put(k, ctl); put(k, nsys); put(k, cond); put(k, use_cond);
-  return k;
 }
 
 KernelCall thermo_call(const SysDev* d, const Tile* tiles_s, int nsys, GroupCtl*) {

@@ -29,8 +29,6 @@ inline void args_of(const KernelCall& k, void** a) {
 // integrate (K6): kick(s) + drift + wrap + fixed-point shadow + displacement check;
 // the last block decides per-system activity/rebuild/sort for the step and, when
 // use_cond, sets the graph conditional that gates the rebuild.
-KernelCall integrate_call(int prec, const SysDev* d, const Tile* tiles, int ntiles, GroupCtl* ctl,
-                          int nsys, cudaGraphConditionalHandle cond, int use_cond);
 // cell list + sort + neighbour list (each a no-op for systems not rebuilding)
 KernelCall bin_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
 KernelCall scan_call(const SysDev* d, const Tile* tiles_s, int nsys, GroupCtl* ctl);
@@ -42,15 +40,24 @@ KernelCall copyback_call(const SysDev* d, const Tile* tiles_p, int ntiles, Group
 KernelCall blocks_call(const SysDev* d, const Tile* tiles_b, int ntiles, GroupCtl* ctl);
 KernelCall nlist_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl* ctl, bool rel,
                       bool multi, bool staged);
-// pair force (K5): ev = 0 forces only, 1 also energy/virial partial sums
-// (+ per-particle arrays when the descriptor has them); force_all ignores the
-// per-step activity flag (used outside the step graph)
-KernelCall force_call(int prec, int multi, int ev, int tpp, int block, const SysDev* d,
-                      const Tile* tiles_f, int ntiles, GroupCtl* ctl, int force_all);
+// pair force kernels.  MODE_FORCE: forces at the current positions (readouts);
+// MODE_EV: also energy / virial / v.v partial sums (+ per-particle arrays when the
+// descriptor has them); MODE_STEP: the step kernel -- forces, the velocity Verlet
+// update of every particle into the next shadow buffer, and the end-of-step
+// decisions by the last of sa.total_blocks blocks over the step's force launches.
+enum { MODE_FORCE = 0, MODE_EV = 1, MODE_STEP = 2 };
+struct StepArgs {
+  int nsys = 0;             // systems of the group (decisions of the last block)
+  int total_blocks = 0;     // blocks of all the step's force launches
+  cudaGraphConditionalHandle cond = 0;   // the rebuild conditional of the step graph
+  int use_cond = 0;
+};
+KernelCall force_call(int prec, int multi, int mode, int tpp, int block, const SysDev* d,
+                      const Tile* tiles_f, int ntiles, GroupCtl* ctl, const StepArgs& sa);
 // staged pair force: one kernel block per 2x2x2 cell block, window in shared memory
 // (mixed precision); part_base = first partial-sum slot of these tiles
-KernelCall force_staged_call(int multi, int ev, const SysDev* d, const Tile* tiles_s, int ntiles,
-                             GroupCtl* ctl, int force_all, int part_base, int window_cap);
+KernelCall force_staged_call(int multi, int mode, const SysDev* d, const Tile* tiles_s, int ntiles,
+                             GroupCtl* ctl, int part_base, int window_cap, const StepArgs& sa);
 constexpr int STAGED_BLOCK = 256;
 // thermo reduction (K7), one block per system
 KernelCall thermo_call(const SysDev* d, const Tile* tiles_s, int nsys, GroupCtl* ctl);
