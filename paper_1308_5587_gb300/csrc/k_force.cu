@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
   const int i = t.first + (valid ? g : 0);
   if (active) {
   const int n = valid ? s.nn[i] : 0;
+  if (STEP && valid && h == 0) prefetch_particle(s, i);   // in flight during the gathers
   const int groups = (n + 3) >> 2;
   const int4* __restrict__ nl4 = reinterpret_cast<const int4*>(s.nl) + i;
   const size_t stride = (size_t)s.nl_stride;
@@ -213,7 +214,8 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
     if (STEP) {   // the step needs no stored force: each lane-0 integrates its particle
       if (valid && h == 0) {
         const double f[3] = {widen_f32(Fx, bad), widen_f32(Fy, bad), widen_f32(Fz, bad)};
-        integrate_one<PREC>(s, i, qi.w, f, fw.v_full, q_at(s, step + 1), nullptr, need, bad);
+        integrate_one<PREC>(s, i, qi.w, f, fw.v_full, load_particle(s, i), q_at(s, step + 1), nullptr,
+                            need, bad);
       }
     } else if (valid && h == 0) {
       s.f32[i] = make_float4(Fx, Fy, Fz, EV ? E : 0.f);
@@ -291,7 +293,8 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
       if (valid && h == 0) {
         const double f[3] = {fx, fy, fz};
         bad |= !isfinite(fx) || !isfinite(fy) || !isfinite(fz);
-        integrate_one<PREC>(s, i, ti, f, fw.v_full, q_at(s, step + 1), p64_at(s, step + 1), need, bad);
+        integrate_one<PREC>(s, i, ti, f, fw.v_full, load_particle(s, i), q_at(s, step + 1),
+                            p64_at(s, step + 1), need, bad);
       }
     } else if (valid && h == 0) {
       s.f64[i] = make_double4_32a(fx, fy, fz, EV ? e : 0.0);
@@ -428,7 +431,8 @@ __global__ void __launch_bounds__(STAGED_BLOCK) k_force_staged(const SysDev* __r
     const float Fx = fx.x + fx.y, Fy = fy.x + fy.y, Fz = fz.x + fz.y;
     if (STEP) {
       const double f[3] = {widen_f32(Fx, bad), widen_f32(Fy, bad), widen_f32(Fz, bad)};
-      integrate_one<GBMD_MIXED>(s, i, qi.w, f, vfull, q_at(s, step + 1), nullptr, need, bad);
+      integrate_one<GBMD_MIXED>(s, i, qi.w, f, vfull, load_particle(s, i), q_at(s, step + 1), nullptr,
+                                need, bad);
     } else {
       s.f32[i] = make_float4(Fx, Fy, Fz, EV ? e.x + e.y : 0.f);
     }

@@ -41,29 +41,51 @@ __device__ __forceinline__ long long rint_ll(double x) {
   return __double_as_longlong(m) - 0x4338000000000000LL;
 }
 
+// the lines of the particle's state that the integration reads, requested into L2
+// before the force loop (no registers held through the loop)
+__device__ __forceinline__ void prefetch_particle(const SysDev& s, int i) {
+  const int n = s.n;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(s.x + a * n + i));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(s.v + a * n + i));
+  }
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(s.q_build + i));
+}
+
+// the particle's state the integration reads
+struct ParticleState {
+  double v[3], xq[3];
+  int4 qb;   // shadow at the last list build
+};
+__device__ __forceinline__ ParticleState load_particle(const SysDev& s, int i) {
+  ParticleState p;
+  const int n = s.n;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    p.v[a] = s.v[a * n + i];
+    p.xq[a] = s.x[a * n + i];
+  }
+  p.qb = __ldg(s.q_build + i);
+  return p;
+}
+
 // one particle's kick, drift, wrap and new shadow; `need` = it moved more than
 // r_buff/2 since the last list build
 template <int PREC>
 __device__ __forceinline__ void integrate_one(const SysDev& s, int i, int ty, const double f[3],
-                                              int vfull, int4* __restrict__ q_next,
+                                              int vfull, const ParticleState& p0,
+                                              int4* __restrict__ q_next,
                                               double4_32a* __restrict__ p64_next, bool& need,
                                               bool& bad) {
   const int n = s.n;
-  double* __restrict__ xp = s.x;
-  double* __restrict__ vp = s.v;
   const double kick = vfull ? s.h : s.h + s.h;
   double v[3], xq[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    v[a] = vp[a * n + i];
-    xq[a] = xp[a * n + i];
-  }
-  const int4 qb = __ldg(s.q_build + i);
   int q[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    v[a] = fma(kick, f[a], v[a]);
-    xq[a] = fma(s.dtq[a], v[a], xq[a]);
+    v[a] = fma(kick, f[a], p0.v[a]);
+    xq[a] = fma(s.dtq[a], v[a], p0.xq[a]);
     long long qq = rint_ll(xq[a]);
     const long long k = (qq + 0x80000000LL) >> 32;       // floor((xq + 2^31) / 2^32)
     if (k != 0) {
@@ -76,8 +98,8 @@ __device__ __forceinline__ void integrate_one(const SysDev& s, int i, int ty, co
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    vp[a * n + i] = v[a];
-    xp[a * n + i] = xq[a];
+    s.v[a * n + i] = v[a];
+    s.x[a * n + i] = xq[a];
   }
   q_next[i] = make_int4(q[0], q[1], q[2], ty);
   if (PREC == GBMD_FP64)
@@ -85,9 +107,9 @@ __device__ __forceinline__ void integrate_one(const SysDev& s, int i, int ty, co
                                    xq[1] * (s.L[1] * (1.0 / 4294967296.0)),
                                    xq[2] * (s.L[2] * (1.0 / 4294967296.0)),
                                    __longlong_as_double(ty));
-  const float dx = (float)min_image_fixed(q[0], qb.x) * s.fscale[0];
-  const float dy = (float)min_image_fixed(q[1], qb.y) * s.fscale[1];
-  const float dz = (float)min_image_fixed(q[2], qb.z) * s.fscale[2];
+  const float dx = (float)min_image_fixed(q[0], p0.qb.x) * s.fscale[0];
+  const float dy = (float)min_image_fixed(q[1], p0.qb.y) * s.fscale[1];
+  const float dz = (float)min_image_fixed(q[2], p0.qb.z) * s.fscale[2];
   need = dx * dx + dy * dy + dz * dz > s.rbuff_half2;
 }
 
