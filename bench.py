@@ -4,8 +4,9 @@
 Workload (default): the 64,000-particle Lennard-Jones fluid, rho 0.84, T 1.2,
 r_cut 2.5 sigma (energy-shifted), r_buff 0.4, dt 0.005, mixed precision (FP32 pair
 forces, FP64 positions/integration/reductions), seeded synthetic FCC+jitter input.
-A "step" is one velocity-Verlet time step of the whole path: integrate (+ the
-rebuild check), the conditional cell-list/neighbour-list rebuild, the pair force.
+A "step" is one velocity-Verlet time step of the whole path: the step kernel (pair
+force, then kick, drift, wrap, shadow and the rebuild check) and the conditional
+cell-list/neighbour-list rebuild that follows it.
 
 Timing: W untimed warm-up steps, then exactly K steps, each bracketed by CUDA
 events on the system's stream, with a 256 MB write between steps so that every

@@ -3,10 +3,10 @@
 //
 // A "group" is the unit that is stepped: one system alone, or a batch of systems.
 // Its step is a CUDA graph per block of steps; per step:
-//   integrate (K6) -> IF(any system needs a rebuild) { bin -> scan -> scatter ->
-//   cellsort -> permute -> copyback -> nlist } -> force (K5).
-// The IF is a graph conditional node whose value the integrate kernel's last block
-// sets on the device, so a step never returns to the host.
+//   step kernel (pair force K5 + integration K6) -> IF(any system needs a rebuild)
+//   { bin -> scan -> scatter -> cellsort -> permute -> copyback -> [blocks] -> nlist }.
+// The IF is a graph conditional node whose value the step kernel's last block sets
+// on the device, so a step never returns to the host.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>

@@ -40,7 +40,7 @@ enum DevError : int { DEV_OK = 0, DEV_OVERFLOW = 1, DEV_NONFINITE = 2, DEV_BADTY
 constexpr int WIN_CELLS = 64;
 
 struct Flags {
-  int rebuild_req;          // set by the integrate kernel when r_buff/2 is exceeded
+  int rebuild_req;          // set by the step kernel when r_buff/2 is exceeded
   int do_rebuild;           // this step rebuilds (decided once per step)
   int do_sort;              // this step re-sorts (Morton cell order) before building
   int active;               // this step advances the system

@@ -26,9 +26,6 @@ inline void args_of(const KernelCall& k, void** a) {
   for (int i = 0; i < k.nargs; ++i) a[i] = const_cast<unsigned char*>(k.store[i]);
 }
 
-// integrate (K6): kick(s) + drift + wrap + fixed-point shadow + displacement check;
-// the last block decides per-system activity/rebuild/sort for the step and, when
-// use_cond, sets the graph conditional that gates the rebuild.
 // cell list + sort + neighbour list (each a no-op for systems not rebuilding)
 KernelCall bin_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
 KernelCall scan_call(const SysDev* d, const Tile* tiles_s, int nsys, GroupCtl* ctl);
