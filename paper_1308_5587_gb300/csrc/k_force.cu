@@ -26,6 +26,10 @@
 // sums are FP32.
 // FP64: positions come from the double4 shadow p64; the minimum image is one
 // conditional correction by L (|d| < L for wrapped coordinates); all arithmetic FP64.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "launch.cuh"
 #include "step_core.cuh"
 
@@ -513,10 +517,14 @@ KernelCall force_staged_call(int multi, int mode, const SysDev* d, const Tile* t
   const int md = mode < 0 ? 0 : mode > 2 ? 2 : mode;
   void* f = fs[mt][md];
   const size_t smem = (size_t)window_cap * 3 * sizeof(int);
-  static bool attr_set[3][3] = {};
-  if (!attr_set[mt][md]) {   // dynamic shared memory above the 48 KB default
-    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr_set[mt][md] = true;
+  {   // dynamic shared memory above the 48 KB default: once per kernel and device
+    static std::mutex mu;
+    static std::set<std::pair<int, void*>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.insert({dev, f}).second)
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   }
   KernelCall k = make_call(f, ntiles, STAGED_BLOCK, smem);
   put(k, d); put(k, tiles_s); put(k, ctl); put(k, part_base); put(k, sa.nsys);
