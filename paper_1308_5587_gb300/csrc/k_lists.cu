@@ -374,7 +374,8 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
 
   // candidate c of the flattened stream into registers (every lane runs every
   // shuffle); written to the chunk arrays by stage() once the previous chunk is done
-  int4 nq = make_int4(0, 0, 0, -1);
+  int4 nq = make_int4(0, 0, 0, 0);   // w = j | type << 30 (types 2, 3 set the sign bit)
+  bool nempty = true;                // past the end of the stream
   int nloc = 0;
   auto fetch = [&](int c) {
     int lo = 0;
@@ -387,8 +388,9 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     const int st = __shfl_sync(0xffffffffu, sc_start, lo);
     const int ex = __shfl_sync(0xffffffffu, excl, lo);
     if (STAGED) nloc = __shfl_sync(0xffffffffu, sc_woff, lo) + (c - ex);
-    if (c >= total) {
-      nq = make_int4(0, 0, 0, -1);
+    nempty = c >= total;
+    if (nempty) {
+      nq = make_int4(0, 0, 0, 0);
       return;
     }
     const int j = members[st + (c - ex)];
@@ -397,7 +399,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   };
   auto stage = [&]() {
     if (REL) {   // an empty slot sits far away: never within range
-      const bool none = nq.w < 0;
+      const bool none = nempty;
       cxs[w][lane] = none ? 1e18f : (float)min_image_fixed(nq.x, ox) * fs0;
       cys[w][lane] = none ? 1e18f : (float)min_image_fixed(nq.y, oy) * fs1;
       czs[w][lane] = none ? 1e18f : (float)min_image_fixed(nq.z, oz) * fs2;

@@ -65,6 +65,7 @@ def _desc(lib, **over):
     (dict(pos=np.full((4, 3), np.nan)), "BAD_ARG"),
     (dict(threads_per_particle=3), "BAD_ARG"),
     (dict(force_path=2), "BAD_ARG"),
+    (dict(n=0), "BAD_ARG"),                                           # empty system
     (dict(eps=np.array([[1.0, 2.0], [1.5, 1.0]])), "BAD_ARG"),     # not symmetric
 ])
 def test_create_rejects_bad_arguments_on_the_host(lib, bad, status):

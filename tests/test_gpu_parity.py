@@ -458,3 +458,30 @@ def test_autotune_picks_a_valid_cell_width_and_tuning():
     Fo, _, _, _, _ = oracle.forces(pos, w.box, w.types, w.pairs.as_dict())
     assert rel_l2(s.forces(), Fo) <= 1e-5
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_four_types_pair_table_path(prec):
+    """Four particle types (the pair table read from shared memory rather than held in
+    registers, in the force kernels and the list build): forces, energy and virial
+    after stepping, and the neighbour sets, against the oracle."""
+    base = wl.lj_fluid(1500, 0.9, 1.2, seed=35)
+    rng = np.random.default_rng(35)
+    types = rng.integers(0, 4, base.n).astype(np.int32)
+    a = np.arange(4)
+    eps = 0.6 + 0.2 * (a[:, None] + a[None, :])
+    sigma = 0.85 + 0.05 * np.abs(a[:, None] - a[None, :])
+    pairs = wl.PairTable(eps, sigma, 2.5 * sigma)
+    w = wl.Workload(base.pos, base.vel, types, base.box, pairs, r_buff=0.4)
+    s = gbmd.System.from_workload(w, precision=prec)
+    s.step(25)
+    check_forces(s, w, prec, "four types")
+    s.set_state(*s.state())          # lists rebuilt at the current positions
+    pos = s.state()[0]
+    rl = pairs.rcut + w.r_buff
+    pr, r = oracle.neighbors(pos, w.box, types, rl)
+    ok = np.abs(r - rl[types[pr[:, 0]], types[pr[:, 1]]]) > 1e-9
+    ref = {(int(x), int(y)) for x, y in pr[ok]}
+    band = {(int(x), int(y)) for x, y in pr[~ok]}
+    assert _pairs_of(s, w.n) - band == ref
+    s.close()
