@@ -485,3 +485,64 @@ def test_four_types_pair_table_path(prec):
     band = {(int(x), int(y)) for x, y in pr[~ok]}
     assert _pairs_of(s, w.n) - band == ref
     s.close()
+
+
+def _four_type_workload(n, seed):
+    base = wl.lj_fluid(n, 0.9, 1.2, seed=seed)
+    types = np.random.default_rng(seed).integers(0, 4, base.n).astype(np.int32)
+    a = np.arange(4)
+    sigma = 0.85 + 0.05 * np.abs(a[:, None] - a[None, :])
+    pairs = wl.PairTable(0.6 + 0.2 * (a[:, None] + a[None, :]), sigma, 2.5 * sigma)
+    return wl.Workload(base.pos, base.vel, types, base.box, pairs, r_buff=0.4)
+
+
+def test_batch_of_mixed_shapes_and_paths_equals_alone():
+    """One batch holding a single-type system, a Kob-Andersen system, a four-type
+    system and a system on the staged force path: two force launches share the
+    step's last-block count, and the pair-table mode is the batch's widest.  Every
+    member ends bitwise where it ends alone."""
+    ws = [wl.lj_fluid(1200, 0.84, 1.2, seed=71),
+          wl.lj_fluid(1500, 1.2, 1.0, seed=72, binary=True, r_buff=0.3),
+          _four_type_workload(1000, 73),
+          wl.lj_fluid(6000, 0.84, 1.2, seed=74)]
+    paths = ["global", "global", "global", "staged"]
+    alone = []
+    for w, fp in zip(ws, paths):
+        s = gbmd.System.from_workload(w, precision="mixed", force_path=fp)
+        s.set_tuning(2, 128)
+        s.step(60)
+        alone.append((s.state(), s.forces()))
+        s.close()
+    b = gbmd.Batch("mixed")
+    b.set_tuning(2, 128)
+    sys_ = [gbmd.System.from_workload(w, precision="mixed", force_path=fp)
+            for w, fp in zip(ws, paths)]
+    assert sys_[3].info()["force_path"] == 1
+    for s in sys_:
+        b.add(s)
+    b.step(60)
+    b.sync()
+    for s, (st, F) in zip(sys_, alone):
+        st2 = s.state()
+        assert st2[3] == 60
+        for k in range(3):
+            assert np.array_equal(np.asarray(st2[k]), np.asarray(st[k]))
+        assert np.array_equal(s.forces(), F)
+    b.close()
+    for s in sys_:
+        s.close()
+
+
+def test_staged_path_four_types():
+    w = _four_type_workload(6000, 75)
+    a = gbmd.System.from_workload(w, precision="mixed", force_path="staged")
+    g = gbmd.System.from_workload(w, precision="mixed", force_path="global")
+    assert a.info()["force_path"] == 1
+    a.step(30)
+    g.step(30)
+    pa, pg = a.state()[0], g.state()[0]
+    assert np.abs(mi(pa - pg, w.box)).max() < 1e-4
+    Fo, *_ = oracle.forces(pa, w.box, w.types, w.pairs.as_dict())
+    assert rel_l2(a.forces(), Fo) <= 1e-5
+    a.close()
+    g.close()
