@@ -546,3 +546,41 @@ def test_staged_path_four_types():
     assert rel_l2(a.forces(), Fo) <= 1e-5
     a.close()
     g.close()
+
+
+def test_overflow_inside_a_batch_is_recovered_bitwise():
+    """A batch member whose list overflows mid-run (the inflowing lattice gas) is
+    frozen on the device while the others keep stepping, grown and caught up at the
+    batch's sync; every member equals its roomy run alone."""
+    g = (np.arange(12) - 5.5) * 1.5
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    box = np.full(3, 18.0)
+    vel = -0.6 * pos / 9.0
+    other = wl.lj_fluid(2000, 0.84, 1.2, seed=76)
+    roomy = gbmd.System(pos, vel, box, precision="mixed", nlist_capacity=400)
+    c0 = int(roomy.neighbors(cap=400)[0].max())
+    roomy.set_tuning(2, 128)
+    roomy.step(300)
+    ref_gas = roomy.state()
+    o = gbmd.System.from_workload(other, precision="mixed")
+    o.set_tuning(2, 128)
+    o.step(300)
+    ref_other = o.state()
+    roomy.close()
+    o.close()
+    b = gbmd.Batch("mixed")
+    b.set_tuning(2, 128)
+    tight = gbmd.System(pos, vel, box, precision="mixed", nlist_capacity=c0)
+    o2 = gbmd.System.from_workload(other, precision="mixed")
+    b.add(tight)
+    b.add(o2)
+    b.step(300)
+    b.sync()
+    assert tight.info()["nlist_capacity"] > c0
+    for got, ref in ((tight.state(), ref_gas), (o2.state(), ref_other)):
+        assert got[3] == 300
+        for k in range(3):
+            assert np.array_equal(np.asarray(got[k]), np.asarray(ref[k]))
+    b.close()
+    tight.close()
+    o2.close()
