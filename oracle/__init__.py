@@ -61,6 +61,9 @@ def _bind(lib):
                               C.c_double, i64, dp, vp, vp]
     lib.oracle_thermo.argtypes = [i64, dp, C.c_double, dp, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]
+    lib.oracle_nvt.argtypes = [i64, dp, dp, dp, ip, ip, i32, dp, dp, dp, C.c_double,
+                               C.c_double, C.c_double, C.c_double, i64, dp,
+                               C.POINTER(C.c_double), C.POINTER(C.c_double), vp, vp, vp, vp]
     return lib
 
 
@@ -204,4 +207,29 @@ def vv_run(pos, vel, box, types, params, mass, dt, nsteps, image=None, series=Fa
     out = dict(pos=pos, vel=vel, image=image, force=F)
     if series:
         out["pe"], out["ke"] = pe, ke
+    return out
+
+
+def nvt_run(pos, vel, box, types, params, mass, dt, kT, tau, nsteps, xi=0.0, eta=0.0,
+            image=None, series=False, lib=None):
+    """Nose-Hoover (MTK) NVT run.  Returns dict(pos, vel, image, force, xi, eta
+    [, pe, ke, xis, etas]); H = K + U + g kT (tau^2 xi^2 / 2 + eta), g = 3N - 3, is
+    its conserved quantity."""
+    lib = lib or load()
+    pos, box, n, types, nt = _common(pos, box, types, params)
+    pos = pos.copy()
+    vel = np.array(vel, np.float64).reshape(-1, 3)
+    image = np.zeros((n, 3), np.int32) if image is None else np.array(image, np.int32)
+    eps, sig, rc = _pair_tables(params, nt)
+    F = np.zeros((n, 3))
+    ser = [np.zeros(nsteps + 1) if series else None for _ in range(4)]
+    x, e = C.c_double(xi), C.c_double(eta)
+    rcode = lib.oracle_nvt(n, box, pos, vel, image, types, nt, eps, sig, rc, float(mass),
+                           float(dt), float(kT), float(tau), int(nsteps), F, C.byref(x),
+                           C.byref(e), *[_ptr(a) for a in ser])
+    if rcode:
+        raise ValueError(f"oracle_nvt failed ({rcode})")
+    out = dict(pos=pos, vel=vel, image=image, force=F, xi=x.value, eta=e.value)
+    if series:
+        out["pe"], out["ke"], out["xis"], out["etas"] = ser
     return out

@@ -299,6 +299,68 @@ int oracle_vv(int64_t n, const double *box, double *pos, double *vel, int32_t *i
     return 0;
 }
 
+/* NVT with a Nose-Hoover thermostat in the Martyna-Tobias-Klein form (Section 3.1:
+ * the NVT, NPH and NPT integrators follow Martyna, Tobias and Klein; Listing 1 uses
+ * NVT with kT and tau).  The paper prints no equation; the textbook equations are
+ *   dx/dt = v,  dv/dt = F/m - xi v,  dxi/dt = (2K/(g kT) - 1) / tau^2,  deta/dt = xi
+ * with g = 3N - 3 degrees of freedom (the temperature convention used here), and
+ *   H = K + U + g kT (tau^2 xi^2 / 2 + eta)
+ * is conserved.  One step of the time-reversible splitting:
+ *   xi += dt/2 G(K);  v *= exp(-xi dt/2);  eta += dt/2 xi;
+ *   v += dt/(2m) F;  x += dt v;  wrap;  F = F(x);  v += dt/(2m) F;
+ *   v *= exp(-xi dt/2);  eta += dt/2 xi;  xi += dt/2 G(K)
+ * with G(K) = (2K/(g kT) - 1)/tau^2 and K from the velocities of that moment.
+ * xi_io / eta_io hold the thermostat on entry and on return; the optional series
+ * (nsteps + 1 entries) record U, K, xi, eta after each step (entry 0: the start). */
+int oracle_nvt(int64_t n, const double *box, double *pos, double *vel, int32_t *image,
+               const int32_t *type, int32_t ntypes, const double *eps, const double *sigma,
+               const double *rcut, double mass, double dt, double kT, double tau,
+               int64_t nsteps, double *force, double *xi_io, double *eta_io, double *pe,
+               double *ke, double *xis, double *etas)
+{
+    if (check_common(n, box, ntypes) || nsteps < 0 || !(mass > 0) || !(kT > 0) || !(tau > 0) ||
+        n < 2 || !xi_io || !eta_io)
+        return -1;
+    const double g = 3.0 * (double)n - 3.0;
+    double xi = *xi_io, eta = *eta_io;
+    oracle_wrap(n, box, pos, image);
+    double U;
+    int rc = oracle_forces(n, box, pos, type, ntypes, eps, sigma, rcut, force, &U, NULL, NULL,
+                           NULL);
+    if (rc) return rc;
+    if (pe) pe[0] = U;
+    if (ke) ke[0] = oracle_kinetic(n, vel, mass);
+    if (xis) xis[0] = xi;
+    if (etas) etas[0] = eta;
+    const double h = 0.5 * dt / mass;
+    for (int64_t s = 1; s <= nsteps; ++s) {
+        double K = oracle_kinetic(n, vel, mass);
+        xi += 0.5 * dt * (2.0 * K / (g * kT) - 1.0) / (tau * tau);
+        double sc = exp(-0.5 * dt * xi);
+        for (int64_t i = 0; i < 3 * n; ++i) vel[i] *= sc;
+        eta += 0.5 * dt * xi;
+        for (int64_t i = 0; i < 3 * n; ++i) vel[i] += h * force[i];
+        for (int64_t i = 0; i < 3 * n; ++i) pos[i] += dt * vel[i];
+        oracle_wrap(n, box, pos, image);
+        rc = oracle_forces(n, box, pos, type, ntypes, eps, sigma, rcut, force, &U, NULL, NULL,
+                           NULL);
+        if (rc) return rc;
+        for (int64_t i = 0; i < 3 * n; ++i) vel[i] += h * force[i];
+        sc = exp(-0.5 * dt * xi);
+        for (int64_t i = 0; i < 3 * n; ++i) vel[i] *= sc;
+        eta += 0.5 * dt * xi;
+        K = oracle_kinetic(n, vel, mass);
+        xi += 0.5 * dt * (2.0 * K / (g * kT) - 1.0) / (tau * tau);
+        if (pe) pe[s] = U;
+        if (ke) ke[s] = K;
+        if (xis) xis[s] = xi;
+        if (etas) etas[s] = eta;
+    }
+    *xi_io = xi;
+    *eta_io = eta;
+    return 0;
+}
+
 /* T = 2K/(3N-3) and P = (N T + tr(W)/3) / V from K and the virial (paper silent) */
 void oracle_thermo(int64_t n, const double *box, double ke, const double *virial, double *T,
                    double *P)

@@ -13,7 +13,11 @@ index, a transposed operand, a wrong wrap) fails at least one of them:
 * velocity Verlet against an independent high-order ODE solver, its second
   order convergence, time reversibility, momentum conservation, free flight
   through the periodic boundary, energy conservation;
-* the ideal-gas limit of the pressure.
+* the ideal-gas limit of the pressure;
+* Nose-Hoover (MTK) NVT: the weak-coupling limit is velocity Verlet exactly, the
+  extended energy is conserved at second order in dt, the splitting is time
+  reversible under (v, xi) -> (-v, -xi), and the thermostat drives the
+  temperature to kT where NVE would not.
 """
 import json
 import math
@@ -309,3 +313,67 @@ def test_oracle_thread_count_independent(oracle):
     finally:
         oracle.set_threads(old)
     assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+
+
+# --- Nose-Hoover (MTK) NVT -------------------------------------------------------
+
+def _h_ext(r, n, kT, tau):
+    g = 3 * n - 3
+    return r["ke"] + r["pe"] + g * kT * (0.5 * tau * tau * r["xis"] ** 2 + r["etas"])
+
+
+def test_nvt_weak_coupling_is_velocity_verlet(oracle):
+    w = wl.lj_fluid(108, 0.84, 1.2, seed=5)
+    p = w.pairs.as_dict()
+    a = oracle.nvt_run(w.pos, w.vel, w.box, None, p, 1.0, 0.005, 1.2, 1e12, 60)
+    b = oracle.vv_run(w.pos, w.vel, w.box, None, p, 1.0, 0.005, 60)
+    assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["vel"], b["vel"])
+    assert abs(a["xi"]) < 1e-20
+
+
+def _cluster():
+    # four particles near the pair minimum, far from every cut-off and image
+    pos = np.array([[0.0, 0.0, 0.0], [1.12, 0.0, 0.0], [0.56, 0.97, 0.0], [0.56, 0.32, 0.91]])
+    vel = np.random.default_rng(8).normal(scale=0.3, size=(4, 3))
+    vel -= vel.mean(0)
+    return pos, vel, np.full(3, 30.0)
+
+
+def test_nvt_extended_energy_is_conserved_at_second_order(oracle):
+    pos, vel, box = _cluster()
+    p = pair_params()
+    kT, tau, t_end = 0.5, 0.2, 0.4
+    drift = []
+    for dt in (0.004, 0.002):
+        r = oracle.nvt_run(pos, vel, box, None, p, 1.0, dt, kT, tau, int(round(t_end / dt)),
+                           series=True)
+        H = _h_ext(r, 4, kT, tau)
+        drift.append(np.abs(H - H[0]).max())
+        assert abs(r["xi"]) > 1e-3          # the thermostat did act
+    ratio = drift[0] / drift[1]
+    assert 3.0 < ratio < 5.5, ratio         # second order: 4
+
+
+def test_nvt_time_reversibility(oracle):
+    w = wl.lj_fluid(108, 0.84, 1.2, seed=6)
+    p = w.pairs.as_dict()
+    fwd = oracle.nvt_run(w.pos, w.vel, w.box, None, p, 1.0, 0.005, 0.8, 0.3, 100)
+    back = oracle.nvt_run(fwd["pos"], -fwd["vel"], w.box, None, p, 1.0, 0.005, 0.8, 0.3, 100,
+                          xi=-fwd["xi"], image=fwd["image"])
+    x0, _ = oracle.wrap(w.pos, w.box)
+    d = back["pos"] - x0
+    d -= w.box * np.rint(d / w.box)
+    assert np.abs(d).max() < 1e-9
+    assert np.allclose(back["vel"], -w.vel, rtol=0, atol=1e-9)
+    assert abs(back["xi"]) < 1e-9 and abs(fwd["xi"]) > 1e-2
+
+
+def test_nvt_drives_the_temperature_to_kT(oracle):
+    w = wl.lj_fluid(256, 0.84, 1.0, seed=7)
+    p = w.pairs.as_dict()
+    n, g = w.n, 3 * w.n - 3
+    r = oracle.nvt_run(w.pos, w.vel, w.box, None, p, 1.0, 0.005, 2.0, 0.5, 2000, series=True)
+    T = 2.0 * r["ke"] / g
+    assert abs(T[1000:].mean() - 2.0) < 0.2
+    e = oracle.vv_run(w.pos, w.vel, w.box, None, p, 1.0, 0.005, 2000, series=True)
+    assert 2.0 * e["ke"][1000:].mean() / g < 1.2          # NVE does not heat up
