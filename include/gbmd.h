@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define GBMD_ABI_VERSION 3
+#define GBMD_ABI_VERSION 4
 #define GBMD_MAX_TYPES 4
 
 typedef enum gbmd_status {
@@ -102,9 +102,18 @@ typedef struct gbmd_desc {
                                    expected window fits; a window that outgrows shared
                                    memory at a rebuild switches the system to the global
                                    path for good.  gbmd_get_info reports the path in use. */
+    int32_t integrator;         /* GBMD_NVE (0): velocity Verlet.  GBMD_NVT (1): Nose-Hoover
+                                   thermostat in the Martyna-Tobias-Klein form (Section 3.1;
+                                   Listing 1's md.integrate.nvt(kT, tau)): dv/dt = F/m - xi v,
+                                   dxi/dt = (2K/(g kT) - 1)/tau^2, g = 3N - 3, integrated by
+                                   the time-reversible splitting xi/2, scale/2, velocity
+                                   Verlet, scale/2, xi/2.  NVT uses the global force path. */
+    double kT;                  /* NVT target temperature (> 0) */
+    double tau;                 /* NVT coupling time (> 0) */
 } gbmd_desc;
 
 enum { GBMD_PATH_GLOBAL = 0, GBMD_PATH_STAGED = 1 };
+enum { GBMD_NVE = 0, GBMD_NVT = 1 };
 
 /* Thermodynamic quantities of one system at its current step (FP64). */
 typedef struct gbmd_thermo {
@@ -116,6 +125,9 @@ typedef struct gbmd_thermo {
     double virial[6];   /* W: xx, xy, xz, yy, yz, zz */
     double w;           /* tr W */
     int64_t n_rebuilds; /* neighbour-list builds since creation */
+    double xi;          /* NVT thermostat variable (0 for NVE) */
+    double eta;         /* NVT thermostat position, d eta / dt = xi (0 for NVE) */
+    double h_ext;       /* conserved quantity: K + U, plus g kT (tau^2 xi^2 / 2 + eta) for NVT */
 } gbmd_thermo;
 
 /* Configuration and counters of one system, for diagnostics and benchmarks. */
@@ -248,6 +260,12 @@ int gbmd_autotune(gbmd_system *s, const char *cache_path);
  * sets are unchanged, the order of a particle's neighbours (and so the last bits
  * of its FP32 force) may change.  GBMD_ERR_BAD_ARG outside [1, 4]. */
 int gbmd_set_cell_scale(gbmd_system *s, double scale);
+
+/* NVT: set the thermostat variable xi and position eta, as gbmd_get_thermo
+ * reports them for the state of a completed step (checkpoint/resume: after
+ * gbmd_set_state, before stepping; GBMD_ERR_STATE otherwise).  GBMD_ERR_BAD_ARG for
+ * an NVE system or non-finite values. */
+int gbmd_set_thermostat(gbmd_system *s, double xi, double eta);
 
 /* Set the force kernel's threads per particle (1, 2 or 4) and block size
  * (32..512, a multiple of 32) explicitly. */

@@ -101,6 +101,9 @@ struct Group {
   size_t cap_desc = 0, cap_tp = 0, cap_tf = 0, cap_tc = 0, cap_ts = 0, cap_part = 0;
   size_t cap_tb = 0, cap_tbk = 0, cap_te = 0;
   int window_cap = 0;                        // largest staged window among members
+  bool nvt = false;                          // the members integrate NVT (all or none)
+  double* d_nhpart = nullptr;                // NVT: per-step-tile v.v partial sums
+  size_t cap_nhpart = 0;
   double* d_partials = nullptr;
   GroupCtl* d_ctl = nullptr;
   cudaGraphExec_t exec_many = nullptr, exec_one = nullptr;
@@ -161,6 +164,7 @@ int sync_layout(Group* g) {
   g->multi = 0;
   g->rel = true;
   g->window_cap = 0;
+  g->nvt = !m.empty() && m[0]->h.nvt;
   for (size_t k = 0; k < m.size(); ++k) {
     SysDev d = m[k]->h;
     const int n = d.n;
@@ -172,7 +176,9 @@ int sync_layout(Group* g) {
       for (int b = 0; b < d.nblocks; b += 8) tbk.push_back({(int)k, b, std::min(8, d.nblocks - b), 0});
       g->window_cap = std::max(g->window_cap, d.window_cap);
     } else {
+      d.tile_first_s = (int)tf.size();
       for (int f = 0; f < n; f += per_f) tf.push_back({(int)k, f, std::min(per_f, n - f), 0});
+      d.tile_count_s = (int)tf.size() - d.tile_first_s;
       d.tile_first_f = (int)te.size();   // partial sums come from the energy launches
       for (int f = 0; f < n; f += EV_TILE_P) te.push_back({(int)k, f, std::min(EV_TILE_P, n - f), 0});
       d.tile_count_f = (int)te.size() - d.tile_first_f;
@@ -187,7 +193,11 @@ int sync_layout(Group* g) {
   for (auto& d : desc)
     if (d.staged) d.tile_first_f += (int)te.size();   // staged partial sums follow the global ones
   RET(grow(&g->d_partials, &g->cap_part, 8 * std::max<size_t>(te.size() + tb.size(), 1)));
-  for (auto& d : desc) d.partials = g->d_partials;
+  RET(grow(&g->d_nhpart, &g->cap_nhpart, std::max<size_t>(tf.size(), 1)));
+  for (auto& d : desc) {
+    d.partials = g->d_partials;
+    d.nh_part = g->d_nhpart;
+  }
   RET(grow(&g->d_desc, &g->cap_desc, desc.size()));
   RET(grow(&g->d_tp, &g->cap_tp, tp.size()));
   RET(grow(&g->d_tf, &g->cap_tf, tf.size()));
@@ -288,6 +298,18 @@ std::vector<KernelCall> step_calls(const Group* g, cudaGraphConditionalHandle co
   sa.cond = cond;
   sa.use_cond = use_cond;
   std::vector<KernelCall> v;
+  if (g->nvt) {   // forces + closing half + thermostat, then the opening half and drift
+    StepArgs a = sa;
+    a.total_blocks = g->ntf;
+    a.cond = 0;
+    a.use_cond = 0;
+    v.push_back(force_call(g->precision, g->multi, MODE_NVT_A, g->tpp, g->fblock, g->d_desc, g->d_tf,
+                           g->ntf, g->d_ctl, a));
+    StepArgs b = sa;
+    b.total_blocks = g->ntp;
+    v.push_back(nvt_b_call(g->precision, g->d_desc, g->d_tp, g->ntp, g->d_ctl, b));
+    return v;
+  }
   if (g->ntf > 0)
     v.push_back(force_call(g->precision, g->multi, MODE_STEP, g->tpp, g->fblock, g->d_desc, g->d_tf,
                            g->ntf, g->d_ctl, sa));
@@ -503,6 +525,11 @@ int validate(const gbmd_desc* d, bool device) {
     return fail(GBMD_ERR_BAD_ARG, "threads_per_particle must be 0, 1, 2 or 4");
   if (d->force_path != GBMD_PATH_GLOBAL && d->force_path != GBMD_PATH_STAGED)
     return fail(GBMD_ERR_BAD_ARG, "force_path must be GBMD_PATH_GLOBAL or GBMD_PATH_STAGED");
+  if (d->integrator != GBMD_NVE && d->integrator != GBMD_NVT)
+    return fail(GBMD_ERR_BAD_ARG, "integrator must be GBMD_NVE or GBMD_NVT");
+  if (d->integrator == GBMD_NVT &&
+      (!(d->kT > 0) || !(d->tau > 0) || !std::isfinite(d->kT) || !std::isfinite(d->tau) || d->n < 2))
+    return fail(GBMD_ERR_BAD_ARG, "NVT needs kT > 0, tau > 0 and at least 2 particles");
   const int nt = d->ntypes;
   double rmax = 0;
   for (int a = 0; a < nt; ++a)
@@ -694,7 +721,11 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   h.mass = d->mass;
   h.h = 0.5 * d->dt / d->mass;
   s->rl_max = geo.rl_max;
-  s->want_staged = d->force_path == GBMD_PATH_STAGED;
+  s->want_staged = d->force_path == GBMD_PATH_STAGED && d->integrator == GBMD_NVE;
+  h.nvt = d->integrator == GBMD_NVT;
+  h.kT = d->kT;
+  h.tau = d->tau;
+  h.gdof = 3.0 * (double)n - 3.0;
   h.staged = s->want_staged && staged_ok(h, geo.nc);
   h.window_cap = STAGED_WINDOW_CAP;
   for (int a = 0; a < 3; ++a) {
@@ -748,6 +779,7 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   A((void**)&h.x_alt, N * 24); A((void**)&h.v_alt, N * 24); A((void**)&h.img_alt, N * 12);
   A((void**)&h.type_alt, N * 4); A((void**)&h.tag_alt, N * 4); A((void**)&h.q_alt, N * 16);
   A((void**)&h.thermo, 16 * 8);
+  A((void**)&h.nh, 4 * 8);
   A((void**)&s->d_flags, sizeof(Flags));
   A((void**)&s->d_pos, N * 24); A((void**)&s->d_vel, N * 24); A((void**)&s->d_frc, N * 24);
   A((void**)&s->d_img, N * 12); A((void**)&s->d_type, N * 4); A((void**)&s->d_misc, 64);
@@ -758,9 +790,12 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   rc = setup_cells(s, geo.nc, st);
   if (rc != GBMD_OK) { std::string m = g_err; gbmd_destroy(s); g_err = m; return rc; }
   {
+    const double nh0[4] = {0.0, 0.0, 1.0, 0.0};   // xi, eta, exp(-xi dt/2)
     cudaError_t e5 = cudaMemsetAsync(s->d_flags, 0, sizeof(Flags), st);
     cudaError_t e6 = cudaMemsetAsync(h.nn, 0, N * 4, st);
+    cudaError_t e7 = cudaMemcpyAsync(h.nh, nh0, sizeof(nh0), cudaMemcpyHostToDevice, st);
     cudaError_t e4 = cudaStreamSynchronize(st);
+    if (e7) { gbmd_destroy(s); return fail(GBMD_ERR_CUDA, "thermostat upload failed"); }
     if (e4 || e5 || e6) { gbmd_destroy(s); return fail(GBMD_ERR_CUDA, "clearing the flags failed"); }
   }
   // own group
@@ -844,6 +879,32 @@ int load_state(gbmd_system* s, const double* pos, const double* vel, const int32
     RET(read_flags(s, &after, st));
     if (after.error) return fail(GBMD_ERR_NLIST_OVERFLOW, "neighbour list overflow at creation");
   }
+  return GBMD_OK;
+}
+
+// NVT readout of the thermostat, as the state after the last completed step: the
+// stored xi / eta are those of the step's opening half; the closing half adds
+// dt/2 G(K) to xi and dt/2 xi to eta (nothing right after create / set_state).
+// h_ext = K + U (+ g kT (tau^2 xi^2 / 2 + eta) for NVT) is the conserved quantity.
+int fill_thermostat(gbmd_system* s, const Flags& f, gbmd_thermo* out) {
+  out->xi = 0.0;
+  out->eta = 0.0;
+  out->h_ext = out->ke + out->pe;
+  if (!s->h.nvt) return GBMD_OK;
+  double nh[2];
+  cudaStream_t st = cur_stream(s);
+  CK(cudaMemcpyAsync(nh, s->h.nh, sizeof(nh), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const SysDev& h = s->h;
+  double xi = nh[0], eta = nh[1];
+  if (!f.v_full) {
+    const double G = (2.0 * out->ke / (h.gdof * h.kT) - 1.0) / (h.tau * h.tau);
+    eta += 0.5 * h.dt * xi;
+    xi += 0.5 * h.dt * G;
+  }
+  out->xi = xi;
+  out->eta = eta;
+  out->h_ext += h.gdof * h.kT * (0.5 * h.tau * h.tau * xi * xi + eta);
   return GBMD_OK;
 }
 
@@ -1133,7 +1194,7 @@ int gbmd_destroy(gbmd_system* s) {
   if (s->own) {
     Group* g = s->own;
     destroy_graphs(g);
-    cudaFree(g->d_desc); cudaFree(g->d_tp); cudaFree(g->d_tf); cudaFree(g->d_tc); cudaFree(g->d_te);
+    cudaFree(g->d_desc); cudaFree(g->d_tp); cudaFree(g->d_tf); cudaFree(g->d_tc); cudaFree(g->d_te); cudaFree(g->d_nhpart);
     cudaFree(g->d_ts); cudaFree(g->d_tb); cudaFree(g->d_tbk); cudaFree(g->d_partials);
     cudaFree(g->d_ctl);
     delete g;
@@ -1181,7 +1242,7 @@ int gbmd_get_thermo(gbmd_system* s, gbmd_thermo* out) {
   out->w = t[2] + t[5] + t[7];
   out->pressure = (n * out->temperature + out->w / 3.0) / vol;
   out->n_rebuilds = f.n_rebuilds;
-  return GBMD_OK;
+  return fill_thermostat(s, f, out);
 }
 
 int gbmd_get_per_particle(gbmd_system* s, double* energy, double* virial) {
@@ -1310,6 +1371,24 @@ int gbmd_set_step_limit(gbmd_system* s, int64_t step) {
   return write_flags(s, &f, st);
 }
 
+int gbmd_set_thermostat(gbmd_system* s, double xi, double eta) {
+  if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
+  if (!s->h.nvt) return fail(GBMD_ERR_BAD_ARG, "not an NVT system");
+  if (!std::isfinite(xi) || !std::isfinite(eta)) return fail(GBMD_ERR_BAD_ARG, "non-finite thermostat");
+  RET(use_device(s->device));
+  RET(sync_system(s));
+  cudaStream_t st = cur_stream(s);
+  // the state of a completed step, as gbmd_get_thermo reports it: valid where the
+  // velocities are full-step ones too (after create / set_state, before stepping)
+  Flags f;
+  RET(read_flags(s, &f, st));
+  if (!f.v_full) return fail(GBMD_ERR_STATE, "set the thermostat after gbmd_set_state, before stepping");
+  const double nh[3] = {xi, eta, std::exp(-0.5 * s->h.dt * xi)};
+  CK(cudaMemcpyAsync(s->h.nh, nh, sizeof(nh), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return GBMD_OK;
+}
+
 int gbmd_set_cell_scale(gbmd_system* s, double scale) {
   if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
   RET(use_device(s->device));
@@ -1371,6 +1450,8 @@ int gbmd_batch_add(gbmd_batch* bh, gbmd_system* s, int32_t* slot) {
   RET(use_device(reinterpret_cast<Group*>(bh)->device));
   if (s->batch) return fail(GBMD_ERR_STATE, "system already in a batch");
   if (s->h.precision != b->precision) return fail(GBMD_ERR_BAD_ARG, "precision mismatch");
+  for (auto* m : live(b))
+    if (m->h.nvt != s->h.nvt) return fail(GBMD_ERR_BAD_ARG, "a batch holds NVE or NVT systems, not both");
   if (s->device != b->device) return fail(GBMD_ERR_BAD_ARG, "system and batch are on different devices");
   RET(sync_system(s));
   CK(cudaStreamSynchronize(b->stream));
@@ -1482,7 +1563,7 @@ int gbmd_batch_destroy(gbmd_batch* bh) {
     s->own->stream = s->stream;
   }
   destroy_graphs(b);
-  cudaFree(b->d_desc); cudaFree(b->d_tp); cudaFree(b->d_tf); cudaFree(b->d_tc); cudaFree(b->d_te);
+  cudaFree(b->d_desc); cudaFree(b->d_tp); cudaFree(b->d_tf); cudaFree(b->d_tc); cudaFree(b->d_te); cudaFree(b->d_nhpart);
   cudaFree(b->d_ts); cudaFree(b->d_tb); cudaFree(b->d_tbk); cudaFree(b->d_partials);
   cudaFree(b->d_ctl);
   delete b;
@@ -1581,5 +1662,5 @@ extern "C" int gbmd_get_thermo_noalloc(gbmd_system* s, gbmd_thermo* out) {
   out->w = t[2] + t[5] + t[7];
   out->pressure = (n * out->temperature + out->w / 3.0) / vol;
   out->n_rebuilds = f.n_rebuilds;
-  return GBMD_OK;
+  return fill_thermostat(s, f, out);
 }

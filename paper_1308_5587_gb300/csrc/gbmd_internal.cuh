@@ -109,6 +109,14 @@ struct SysDev {
   int *rmember;            // particle index -> member rank
   int sort_period;
   double dt, h;            // h = dt / (2 m)
+  // NVT (Nose-Hoover, MTK form): nh = {xi, eta, exp(-xi dt/2), 0} on the device;
+  // nh_part: the group's per-step-tile partial sums of v.v; tile_first_s /
+  // tile_count_s: this system's tiles of the step's force launch
+  int nvt;
+  double kT, tau, gdof;    // gdof = 3N - 3
+  double* nh;
+  double* nh_part;
+  int tile_first_s, tile_count_s;
   double dtq[3];           // dt * 2^32 / L: the drift in box-fraction units
   double mass;
   // per type pair
@@ -143,6 +151,7 @@ struct SysDev {
 // group-level control block (one per single system or batch)
 struct GroupCtl {
   unsigned int blocks_done;  // last-block counter of the step kernel
+  unsigned int blocks_done_a;   // last-block counter of the NVT force half
   int any_rebuild;
   unsigned long long launches;
 };

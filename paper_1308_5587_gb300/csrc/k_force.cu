@@ -77,7 +77,8 @@ __device__ void reduce_partials(const double* vals, double* out) {
 }
 
 // v_i . v_i at full step: the stored velocity is half a kick (h F_i) behind unless
-// v_full; F_i is the force just computed (bitwise the stepping kernel's)
+// v_full (and, NVT, before the closing thermostat scaling); F_i is the force just
+// computed (bitwise the stepping kernel's)
 __device__ __forceinline__ double vsq(const SysDev& s, int i, double fx, double fy, double fz,
                                       int vfull) {
   const size_t n = (size_t)s.n;
@@ -86,6 +87,12 @@ __device__ __forceinline__ double vsq(const SysDev& s, int i, double fx, double 
     v0 = fma(s.h, fx, v0);
     v1 = fma(s.h, fy, v1);
     v2 = fma(s.h, fz, v2);
+    if (s.nvt) {   // NVT: and the closing thermostat scaling (the opening one's factor)
+      const double sc = s.nh[2];
+      v0 *= sc;
+      v1 *= sc;
+      v2 *= sc;
+    }
   }
   return v0 * v0 + v1 * v1 + v2 * v2;
 }
@@ -142,16 +149,17 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
                                                const Tile* __restrict__ tiles, GroupCtl* ctl,
                                                int nsys, int total_blocks,
                                                cudaGraphConditionalHandle cond, int use_cond) {
-  constexpr bool EV = MODE == MODE_EV, STEP = MODE == MODE_STEP;
+  constexpr bool EV = MODE == MODE_EV, STEP = MODE == MODE_STEP, NVTA = MODE == MODE_NVT_A;
   const Tile t = tiles[blockIdx.x];
   const SysDev& s = sysv[t.sys];
   if (threadIdx.x == 0 && t.first == 0) atomicAdd(&s.flags->launches, 1ull);
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
   const FlagWords fw = load_flag_words(s.flags);
   const longlong2 sl = load_flag_pair(&s.flags->step);   // (step, step_limit)
-  const bool active = !STEP || (fw.error == 0 && (sl.y < 0 || sl.x < sl.y));   // uniform
+  const bool active = !(STEP || NVTA) || (fw.error == 0 && (sl.y < 0 || sl.x < sl.y));   // uniform
   const long long step = sl.x;
   bool need = false, bad = false;
+  double uu = 0.0;   // NVT: v.v after the closing half
   const int nt = s.ntypes;
   constexpr bool SMEM_TAB = PREC == GBMD_MIXED ? MT == 2 : MT != 0;
   __shared__ PairF tabf[SMEM_TAB ? MAXT2 : 1];
@@ -220,6 +228,12 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
         const double f[3] = {widen_f32(Fx, bad), widen_f32(Fy, bad), widen_f32(Fz, bad)};
         integrate_one<PREC>(s, i, qi.w, f, fw.v_full, load_particle(s, i), q_at(s, step + 1), nullptr,
                             need, bad);
+      }
+    } else if (NVTA) {   // closing half kick and scaling; the second half reads F
+      if (valid && h == 0) {
+        const double f[3] = {widen_f32(Fx, bad), widen_f32(Fy, bad), widen_f32(Fz, bad)};
+        uu = nvt_close(s, i, f, fw.v_full);
+        s.f32[i] = make_float4(Fx, Fy, Fz, 0.f);
       }
     } else if (valid && h == 0) {
       s.f32[i] = make_float4(Fx, Fy, Fz, EV ? E : 0.f);
@@ -300,6 +314,12 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
         integrate_one<PREC>(s, i, ti, f, fw.v_full, load_particle(s, i), q_at(s, step + 1),
                             p64_at(s, step + 1), need, bad);
       }
+    } else if (NVTA) {
+      if (valid && h == 0) {
+        const double f[3] = {fx, fy, fz};
+        uu = nvt_close(s, i, f, fw.v_full);
+        s.f64[i] = make_double4_32a(fx, fy, fz, 0.0);
+      }
     } else if (valid && h == 0) {
       s.f64[i] = make_double4_32a(fx, fy, fz, EV ? e : 0.0);
     }
@@ -316,6 +336,48 @@ __global__ void __launch_bounds__(512) k_force(const SysDev* __restrict__ sysv,
   }
   }   // active
   if (STEP) step_tail(s, sysv, ctl, nsys, total_blocks, cond, use_cond, need, bad);
+  if (NVTA) {
+    if (bad) atomicCAS(&s.flags->error, 0, (int)DEV_NONFINITE);
+    nvt_half_tail(s, sysv, ctl, nsys, total_blocks, uu);
+  }
+}
+
+// NVT, second half of the step (one thread per particle): the opening thermostat
+// scaling and half kick, drift, wrap and next shadow (integrate_one with the kick
+// dt/(2m) on u exp(-xi dt/2)), then the end-of-step decisions.
+template <int PREC>
+__global__ void __launch_bounds__(TILE_P) k_nvt_b(const SysDev* __restrict__ sysv,
+                                                  const Tile* __restrict__ tiles, GroupCtl* ctl,
+                                                  int nsys, int total_blocks,
+                                                  cudaGraphConditionalHandle cond, int use_cond) {
+  const Tile t = tiles[blockIdx.x];
+  const SysDev& s = sysv[t.sys];
+  if (threadIdx.x == 0 && t.first == 0) atomicAdd(&s.flags->launches, 1ull);
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
+  const FlagWords fw = load_flag_words(s.flags);
+  const longlong2 sl = load_flag_pair(&s.flags->step);
+  const bool active = fw.error == 0 && (sl.y < 0 || sl.x < sl.y);
+  bool need = false, bad = false;
+  if (active && (int)threadIdx.x < t.count) {
+    const int i = t.first + threadIdx.x;
+    double f[3];
+    if (PREC == GBMD_FP64) {
+      const double4_32a F = s.f64[i];
+      f[0] = F.x; f[1] = F.y; f[2] = F.z;
+    } else {
+      const float4 F = s.f32[i];
+      f[0] = widen_f32(F.x, bad);
+      f[1] = widen_f32(F.y, bad);
+      f[2] = widen_f32(F.z, bad);
+    }
+    ParticleState p = load_particle(s, i);
+    const double so = s.nh[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p.v[a] *= so;
+    integrate_one<PREC>(s, i, s.type[i], f, 1, p, q_at(s, sl.x + 1),
+                        PREC == GBMD_FP64 ? p64_at(s, sl.x + 1) : nullptr, need, bad);
+  }
+  step_tail(s, sysv, ctl, nsys, total_blocks, cond, use_cond, need, bad);
 }
 
 // ---- staged path: one kernel block per aligned 2x2x2 block of cells ----------------
@@ -472,6 +534,7 @@ static void* pick4(int mode) {
   switch (mode) {
     case MODE_EV: return (void*)k_force<PREC, TPP, MT, MODE_EV>;
     case MODE_STEP: return (void*)k_force<PREC, TPP, MT, MODE_STEP>;
+    case MODE_NVT_A: return (void*)k_force<PREC, TPP, MT, MODE_NVT_A>;
     default: return (void*)k_force<PREC, TPP, MT, MODE_FORCE>;
   }
 }
@@ -503,6 +566,15 @@ KernelCall force_call(int prec, int multi, int mode, int tpp, int block, const S
   void* f = prec == GBMD_FP64 ? pick2<GBMD_FP64>(tpp, multi, mode) : pick2<GBMD_MIXED>(tpp, multi, mode);
   KernelCall k = make_call(f, ntiles, block, 0);
   put(k, d); put(k, tiles_f); put(k, ctl); put(k, sa.nsys); put(k, sa.total_blocks);
+  put(k, sa.cond); put(k, sa.use_cond);
+  return k;
+}
+
+KernelCall nvt_b_call(int prec, const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl,
+                      const StepArgs& sa) {
+  void* f = prec == GBMD_FP64 ? (void*)k_nvt_b<GBMD_FP64> : (void*)k_nvt_b<GBMD_MIXED>;
+  KernelCall k = make_call(f, ntiles, TILE_P, 0);
+  put(k, d); put(k, tiles_p); put(k, ctl); put(k, sa.nsys); put(k, sa.total_blocks);
   put(k, sa.cond); put(k, sa.use_cond);
   return k;
 }

@@ -129,7 +129,10 @@ __global__ void __launch_bounds__(TILE_P) k_export(const SysDev* __restrict__ sy
     if (pos) pos[3 * (size_t)tg + a] = s.x[a * n + i] * (s.L[a] / 4294967296.0);
     if (vel) {
       double v = s.v[a * n + i];
-      if (!vfull) v = fma(s.h, f[a], v);
+      if (!vfull) {
+        v = fma(s.h, f[a], v);
+        if (s.nvt) v *= s.nh[2];   // NVT: the closing thermostat scaling
+      }
       vel[3 * (size_t)tg + a] = v;
     }
     if (image) image[3 * (size_t)tg + a] = s.img[a * n + i];

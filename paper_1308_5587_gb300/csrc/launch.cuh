@@ -42,7 +42,11 @@ KernelCall nlist_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl
 // descriptor has them); MODE_STEP: the step kernel -- forces, the velocity Verlet
 // update of every particle into the next shadow buffer, and the end-of-step
 // decisions by the last of sa.total_blocks blocks over the step's force launches.
-enum { MODE_FORCE = 0, MODE_EV = 1, MODE_STEP = 2 };
+// MODE_NVT_A: the first half of an NVT step -- forces, the closing half kick and
+// thermostat scaling of the previous step, v.v partial sums; the last block updates
+// the thermostat.  nvt_b_call: the second half (opening scaling and kick, drift,
+// shadow, rebuild check, end-of-step decisions).
+enum { MODE_FORCE = 0, MODE_EV = 1, MODE_STEP = 2, MODE_NVT_A = 3 };
 struct StepArgs {
   int nsys = 0;             // systems of the group (decisions of the last block)
   int total_blocks = 0;     // blocks of all the step's force launches
@@ -55,6 +59,8 @@ KernelCall force_call(int prec, int multi, int mode, int tpp, int block, const S
 // (mixed precision); part_base = first partial-sum slot of these tiles
 KernelCall force_staged_call(int multi, int mode, const SysDev* d, const Tile* tiles_s, int ntiles,
                              GroupCtl* ctl, int part_base, int window_cap, const StepArgs& sa);
+KernelCall nvt_b_call(int prec, const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl,
+                      const StepArgs& sa);
 constexpr int STAGED_BLOCK = 256;
 // thermo reduction (K7), one block per system
 KernelCall thermo_call(const SysDev* d, const Tile* tiles_s, int nsys, GroupCtl* ctl);

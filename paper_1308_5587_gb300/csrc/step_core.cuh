@@ -113,6 +113,88 @@ __device__ __forceinline__ void integrate_one(const SysDev& s, int i, int ty, co
   need = dx * dx + dy * dy + dz * dz > s.rbuff_half2;
 }
 
+// NVT, first half at particle i once F_i(x^n) is known: the closing half kick and
+// thermostat scaling of the previous step, u = (v + h F) exp(-xi dt/2) (just u = v
+// right after create / set_state, when v holds full-step velocities); u is stored
+// as the velocity and u.u returned for the kinetic energy.  The scale factor
+// exp(-xi dt/2) is the one the previous step's opening half used (nh[2]).
+__device__ __forceinline__ double nvt_close(const SysDev& s, int i, const double f[3], int vfull) {
+  const int n = s.n;
+  const double sc = s.nh[2];
+  double uu = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double u = s.v[a * n + i];
+    if (!vfull) u = fma(s.h, f[a], u) * sc;
+    s.v[a * n + i] = u;
+    uu = fma(u, u, uu);
+  }
+  return uu;
+}
+
+// FP64 sum over the block in a fixed order (warp shuffles, then the warps in order);
+// the result is valid in thread 0
+__device__ __forceinline__ double block_sum_fixed(double v) {
+  __shared__ double wsum[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) wsum[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wsum[k];
+  __syncthreads();
+  return t;
+}
+
+// End of the NVT force half, every block: publish this block's v.v partial sum and
+// count the arrival; the last block updates every NVT system's thermostat
+// (closing half of the previous step, then opening half of this one, with
+// G = (2K/(g kT) - 1)/tau^2 at the kinetic energy K of the closing velocities):
+//   eta += dt/2 xi;  xi += dt/2 G;     (skipped right after create / set_state)
+//   xi += dt/2 G;    eta += dt/2 xi;   exp(-xi dt/2) for the opening scaling
+__device__ __forceinline__ void nvt_half_tail(const SysDev& s, const SysDev* __restrict__ sysv,
+                                              GroupCtl* ctl, int nsys, int total_blocks,
+                                              double uu) {
+  const double part = block_sum_fixed(uu);
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    s.nh_part[blockIdx.x] = part;
+    __threadfence();
+    last = (atomicAdd(&ctl->blocks_done_a, 1u) == (unsigned)total_blocks - 1u);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int k = 0; k < nsys; ++k) {   // uniform over the block
+    const SysDev& sk = sysv[k];
+    if (!sk.nvt) continue;
+    const FlagWords w = load_flag_words(sk.flags);
+    const longlong2 sl = load_flag_pair(&sk.flags->step);
+    if (!(w.error == 0 && (sl.y < 0 || sl.x < sl.y))) continue;
+    double a = 0.0;   // this system's tiles, strided over the block in a fixed order
+    for (int t = threadIdx.x; t < sk.tile_count_s; t += blockDim.x)
+      a += ((const volatile double*)sk.nh_part)[sk.tile_first_s + t];
+    const double sum = block_sum_fixed(a);
+    if (threadIdx.x == 0) {
+      const double K = 0.5 * sk.mass * sum;
+      const double G = (2.0 * K / (sk.gdof * sk.kT) - 1.0) / (sk.tau * sk.tau);
+      const double hdt = 0.5 * sk.dt;
+      double xi = sk.nh[0], eta = sk.nh[1];
+      if (!w.v_full) {
+        eta += hdt * xi;
+        xi += hdt * G;
+      }
+      xi += hdt * G;
+      eta += hdt * xi;
+      sk.nh[0] = xi;
+      sk.nh[1] = eta;
+      sk.nh[2] = exp(-hdt * xi);
+    }
+  }
+  if (threadIdx.x == 0) ctl->blocks_done_a = 0;
+}
+
 // End of the step, every block of the step's force launches: publish this block's
 // rebuild request / error, count the arrival; the last of `total_blocks` arrivals
 // makes each system's decisions for the next step (step counter, rebuild, re-sort)

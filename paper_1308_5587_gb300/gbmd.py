@@ -40,22 +40,27 @@ class gbmd_desc(C.Structure):
                 ("rcut", C.c_void_p), ("r_buff", C.c_double), ("dt", C.c_double),
                 ("mass", C.c_double), ("precision", C.c_int32), ("sort_period", C.c_int32),
                 ("nlist_capacity", C.c_int32), ("threads_per_particle", C.c_int32),
-                ("stream", C.c_void_p), ("device", C.c_int32), ("force_path", C.c_int32)]
+                ("stream", C.c_void_p), ("device", C.c_int32), ("force_path", C.c_int32),
+                ("integrator", C.c_int32), ("kT", C.c_double), ("tau", C.c_double)]
 
 
 GBMD_PATH_GLOBAL, GBMD_PATH_STAGED = 0, 1
 FORCE_PATHS = {"global": GBMD_PATH_GLOBAL, "staged": GBMD_PATH_STAGED}
+GBMD_NVE, GBMD_NVT = 0, 1
+INTEGRATORS = {"nve": GBMD_NVE, "nvt": GBMD_NVT}
 
 
 class gbmd_thermo(C.Structure):
     _fields_ = [("step", C.c_int64), ("pe", C.c_double), ("ke", C.c_double),
                 ("temperature", C.c_double), ("pressure", C.c_double),
-                ("virial", C.c_double * 6), ("w", C.c_double), ("n_rebuilds", C.c_int64)]
+                ("virial", C.c_double * 6), ("w", C.c_double), ("n_rebuilds", C.c_int64),
+                ("xi", C.c_double), ("eta", C.c_double), ("h_ext", C.c_double)]
 
     def as_dict(self):
         return {"step": self.step, "pe": self.pe, "ke": self.ke, "temperature": self.temperature,
                 "pressure": self.pressure, "virial": list(self.virial), "w": self.w,
-                "n_rebuilds": self.n_rebuilds}
+                "n_rebuilds": self.n_rebuilds, "xi": self.xi, "eta": self.eta,
+                "h_ext": self.h_ext}
 
 
 class gbmd_info(C.Structure):
@@ -95,6 +100,7 @@ _SIGS = {
     "gbmd_autotune": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gbmd_set_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "gbmd_set_cell_scale": (C.c_int, [C.c_void_p, C.c_double]),
+    "gbmd_set_thermostat": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
     "gbmd_batch_create": (C.c_int, [C.c_int32, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "gbmd_batch_add": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "gbmd_batch_remove": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -153,7 +159,8 @@ def _stream_handle(stream):
 
 def make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass, precision,
               sort_period=0, nlist_capacity=0, threads_per_particle=0, stream=None,
-              image=None, device=False, cuda_device=-1, force_path="global"):
+              image=None, device=False, cuda_device=-1, force_path="global", integrator="nve",
+              kT=0.0, tau=0.0):
     """Build a gbmd_desc; returns (desc, keepalive) -- keep the second alive."""
     eps = np.atleast_2d(np.asarray(eps, np.float64))
     nt = eps.shape[0]
@@ -187,6 +194,9 @@ def make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass, preci
     d.stream = _stream_handle(stream)
     d.device = int(cuda_device)
     d.force_path = FORCE_PATHS.get(force_path, force_path) if isinstance(force_path, str) else int(force_path)
+    d.integrator = INTEGRATORS.get(integrator, integrator) if isinstance(integrator, str) else int(integrator)
+    d.kT = float(kT)
+    d.tau = float(tau)
     return d, keep
 
 
@@ -301,6 +311,10 @@ def gbmd_set_cell_scale(h, scale: float):
     return _check(load().gbmd_set_cell_scale(h, float(scale)))
 
 
+def gbmd_set_thermostat(h, xi: float, eta: float):
+    return _check(load().gbmd_set_thermostat(h, float(xi), float(eta)))
+
+
 def gbmd_batch_create(precision, stream=None, cuda_device=-1) -> int:
     h = C.c_void_p()
     p = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
@@ -362,11 +376,11 @@ class System:
     def __init__(self, pos, vel, box, types=None, eps=1.0, sigma=1.0, rcut=2.5, r_buff=0.4,
                  dt=0.005, mass=1.0, precision="mixed", sort_period=0, nlist_capacity=0,
                  threads_per_particle=0, stream=None, image=None, device=False, n=None,
-                 cuda_device=-1, force_path="global"):
+                 cuda_device=-1, force_path="global", integrator="nve", kT=0.0, tau=0.0):
         n = int(n if n is not None else np.asarray(pos).reshape(-1, 3).shape[0])
         desc, keep = make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass,
                                precision, sort_period, nlist_capacity, threads_per_particle,
-                               stream, image, device, cuda_device, force_path)
+                               stream, image, device, cuda_device, force_path, integrator, kT, tau)
         self.n = n
         self.box = np.broadcast_to(np.asarray(box, np.float64), (3,)).copy()
         self.precision = precision
@@ -417,6 +431,9 @@ class System:
 
     def set_cell_scale(self, scale: float):
         gbmd_set_cell_scale(self.handle, scale)
+
+    def set_thermostat(self, xi: float, eta: float):
+        gbmd_set_thermostat(self.handle, xi, eta)
 
     def set_force_events(self, ev_begin, ev_end):
         gbmd_set_force_events(self.handle, ev_begin, ev_end)

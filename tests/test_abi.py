@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.gbmd_abi_version() == 3
+    assert lib.gbmd_abi_version() == 4
 
 
 def _desc(lib, **over):
@@ -66,6 +66,9 @@ def _desc(lib, **over):
     (dict(threads_per_particle=3), "BAD_ARG"),
     (dict(force_path=2), "BAD_ARG"),
     (dict(n=0), "BAD_ARG"),                                           # empty system
+    (dict(integrator=1, kT=0.0, tau=1.0), "BAD_ARG"),                 # NVT without kT
+    (dict(integrator=1, kT=1.0, tau=-1.0), "BAD_ARG"),
+    (dict(integrator=2), "BAD_ARG"),
     (dict(eps=np.array([[1.0, 2.0], [1.5, 1.0]])), "BAD_ARG"),     # not symmetric
 ])
 def test_create_rejects_bad_arguments_on_the_host(lib, bad, status):
