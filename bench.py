@@ -155,7 +155,23 @@ def make_workload(name: str, rank: int):
     if name == "plain4k":
         return wl.plain_fp64_4k(seed), "fp64", 0, \
             "lj_fluid N=4000 rho=0.84 T=1.2 rc=2.5 shifted rbuff=0.4 dt=0.005 fp64"
+    if name in ("paper64k", "paper64k_mixed"):   # Section 5's LJ benchmark, NVT
+        prec = "fp64" if name == "paper64k" else "mixed"
+        return wl.paper_lj_64k(seed), prec, 100, \
+            f"lj_fluid N=64000 rho=0.382 kT=1.2 rc=3.0 shifted rbuff=0.4 dt=0.005 NVT tau=1.0 {prec}"
     raise SystemExit(f"unknown workload {name}")
+
+
+def integrator_kw(w):
+    """integrator arguments of a workload (NVE unless its meta asks for NVT)"""
+    m = w.meta or {}
+    if m.get("integrator") == "nvt":
+        return {"integrator": "nvt", "kT": m["kT"], "tau": m["tau"]}
+    return {}
+
+
+# Section 5: HOOMD-blue v2.6 on one V100, full FP64, this LJ workload (context only)
+PAPER_V100_FP64 = 2.75e8
 
 
 def measured_peaks():
@@ -238,7 +254,7 @@ def e2e_loop(torch, w, precision, sort_period, stream, dev, chunk: int, iters: i
     from paper_1308_5587_gb300 import gbmd
     n = w.n
     s = gbmd.System.from_workload(w, precision=precision, sort_period=sort_period,
-                                  stream=stream, cuda_device=dev)
+                                  stream=stream, cuda_device=dev, **integrator_kw(w))
     pos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     vel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     img = torch.empty((n, 3), dtype=torch.int32, pin_memory=True).numpy()
@@ -327,7 +343,7 @@ def gpu_arm(args):
 
     s = gbmd.System.from_workload(w, precision=precision, sort_period=sort_period,
                                   stream=stream.cuda_stream, cuda_device=local,
-                                  force_path=args.force_path)
+                                  force_path=args.force_path, **integrator_kw(w))
     if args.autotune:
         s.autotune(os.path.join(ROOT, "_work", "tune_cache.txt") if os.path.isdir(
             os.path.join(ROOT, "_work")) else None)
@@ -383,7 +399,8 @@ def gpu_arm(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None,
+           "scaling": "weak",
+           "vs_baseline": (value / PAPER_V100_FP64 if args.workload == "paper64k" else None),
            "dtype": "f32 pair forces + f64 integration" if precision == "mixed" else "f64",
            "data": "synthetic (seeded FCC + jitter, Maxwell-Boltzmann; no dataset)",
            "config": {"workload": wdesc, "n": n, "precision": precision,
@@ -653,7 +670,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["gbmd", "reference"], default="gbmd")
-    ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k", "batch", "serve"],
+    ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k", "paper64k", "paper64k_mixed",
+                                           "batch", "serve"],
                     default="lj64k")
     ap.add_argument("--replicas", type=int, default=256, help="batch workload: replicas")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: fixed tuning")

@@ -143,6 +143,14 @@ def ka_1m(seed: int = BASE_SEED, n: int = 1_000_000) -> Workload:
     return lj_fluid(n, 1.2, 1.0, seed, binary=True, r_buff=0.3)
 
 
+def paper_lj_64k(seed: int = BASE_SEED) -> Workload:
+    """Section 5's LJ benchmark shape: N=64,000, rho 0.382, kT 1.2, r_cut 3.0 (shifted),
+    dt 0.005, NVT with tau 1.0 (Listing 1's coupling time); r_buff 0.4 (not given)."""
+    w = lj_fluid(64000, 0.382, 1.2, seed, pairs=lj_single(rcut=3.0))
+    w.meta.update(integrator="nvt", kT=1.2, tau=1.0)
+    return w
+
+
 def replica_params(count: int = 256, seed: int = BASE_SEED, n_lo: int = 500, n_hi: int = 20000):
     """(N_k, rho_k, T_k, seed_k) for the batched-ensemble shape."""
     rng = np.random.Generator(np.random.PCG64(seed))
