@@ -6,10 +6,16 @@ anything here.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
 CUDA path (``paper_1308_5587_gb300``) and imports nothing from it.
 
 The arithmetic lives in ``lj_oracle.c``; its header states every definition
-(minimum image, energy-shifted LJ, virial, velocity Verlet, brute-force
-neighbour pairs) and which readings the HOOMD-blue paper leaves open
-(Section 3.1 names the LJ pair force, the cell neighbour list and the NVE
-integrator; Section 7.1 names force, energy and virial as what is checked).
+(minimum image, energy-shifted LJ and the other short-range pair potentials
+Section 3.1 lists beside it -- Mie, WCA, Yukawa, Gaussian --, virial, velocity
+Verlet, Nose-Hoover NVT, brute-force neighbour pairs) and which readings the
+HOOMD-blue paper leaves open (Section 3.1 names the LJ pair force, the cell
+neighbour list and the NVE integrator; Section 7.1 names force, energy and virial
+as what is checked).
+
+A pair-parameter dict holds ``eps``, ``sigma``, ``rcut`` (ntypes x ntypes or
+scalars) and optionally ``potential`` ("lj" default, "mie", "wca", "yukawa",
+"gauss"), ``mie_n`` / ``mie_m`` (Mie exponents) and ``kappa`` (Yukawa screening).
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, finite differences, invariants, brute force against an
@@ -50,18 +56,20 @@ def _bind(lib):
     vp = C.c_void_p
     lib.oracle_set_threads.argtypes = [C.c_int]
     lib.oracle_get_threads.restype = C.c_int
-    lib.oracle_forces.argtypes = [i64, dp, dp, ip, i32, dp, dp, dp, dp, vp, vp, vp, vp]
-    lib.oracle_forces_subset.argtypes = [i64, dp, dp, ip, i32, dp, dp, dp, i64, lp, dp, vp, vp]
+    pt = [i32, i32, vp, vp, vp, vp, vp]   # ntypes, kind, eps, sigma, rcut, pa, pb
+    lib.oracle_forces.argtypes = [i64, dp, dp, ip, *pt, dp, vp, vp, vp, vp]
+    lib.oracle_forces_subset.argtypes = [i64, dp, dp, ip, *pt, i64, lp, dp, vp, vp]
+    lib.oracle_cutoffs.argtypes = [*pt, dp]
     lib.oracle_neighbors.argtypes = [i64, dp, dp, ip, i32, dp, i64, vp, vp,
                                      C.POINTER(C.c_int64)]
     lib.oracle_wrap.argtypes = [i64, dp, dp, ip]
     lib.oracle_kinetic.argtypes = [i64, dp, C.c_double]
     lib.oracle_kinetic.restype = C.c_double
-    lib.oracle_vv.argtypes = [i64, dp, dp, dp, ip, ip, i32, dp, dp, dp, C.c_double,
-                              C.c_double, i64, dp, vp, vp]
+    lib.oracle_vv.argtypes = [i64, dp, dp, dp, ip, ip, *pt, C.c_double, C.c_double, i64, dp,
+                              vp, vp]
     lib.oracle_thermo.argtypes = [i64, dp, C.c_double, dp, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]
-    lib.oracle_nvt.argtypes = [i64, dp, dp, dp, ip, ip, i32, dp, dp, dp, C.c_double,
+    lib.oracle_nvt.argtypes = [i64, dp, dp, dp, ip, ip, *pt, C.c_double,
                                C.c_double, C.c_double, C.c_double, i64, dp,
                                C.POINTER(C.c_double), C.POINTER(C.c_double), vp, vp, vp, vp]
     return lib
@@ -81,11 +89,47 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
+POTENTIALS = {"lj": 0, "mie": 1, "wca": 2, "yukawa": 3, "gauss": 4}
+
+
+class _Tables:
+    """The pair model as the C functions take it: (ntypes, kind, eps, sigma, rcut,
+    pa, pb); absent tables are passed as NULL."""
+
+    def __init__(self, params, ntypes):
+        def tab(key):
+            if params.get(key) is None:
+                return None
+            a = np.broadcast_to(np.asarray(params[key], np.float64), (ntypes, ntypes))
+            return np.ascontiguousarray(a).ravel().copy()
+        self.kind = POTENTIALS[params.get("potential", "lj")]
+        self.tables = [tab("eps"), tab("sigma"), tab("rcut")]
+        if self.kind == POTENTIALS["mie"]:
+            self.tables += [tab("mie_n"), tab("mie_m")]
+        elif self.kind == POTENTIALS["yukawa"]:
+            self.tables += [tab("kappa"), None]
+        else:
+            self.tables += [None, None]
+        self.ntypes = ntypes
+
+    def args(self):
+        return [self.ntypes, self.kind, *[_ptr(t) for t in self.tables]]
+
+
 def _pair_tables(params, ntypes):
-    eps = np.ascontiguousarray(np.broadcast_to(params["eps"], (ntypes, ntypes)), np.float64)
-    sig = np.ascontiguousarray(np.broadcast_to(params["sigma"], (ntypes, ntypes)), np.float64)
-    rc = np.ascontiguousarray(np.broadcast_to(params["rcut"], (ntypes, ntypes)), np.float64)
-    return eps.ravel().copy(), sig.ravel().copy(), rc.ravel().copy()
+    return _Tables(params, ntypes)
+
+
+def cutoffs(params, lib=None):
+    """The cut-off radius of every type pair (ntypes x ntypes): the rcut table,
+    except for WCA, whose cut is the LJ minimum 2^(1/6) sigma."""
+    lib = lib or load()
+    nt = int(np.asarray(params["eps"]).shape[0]) if np.ndim(params["eps"]) == 2 else 1
+    t = _Tables(params, nt)
+    out = np.zeros(nt * nt)
+    if lib.oracle_cutoffs(*t.args(), out):
+        raise ValueError("oracle_cutoffs: a table the potential needs is missing")
+    return out.reshape(nt, nt)
 
 
 def _common(pos, box, types, params):
@@ -109,14 +153,14 @@ def forces(pos, box, types, params, lib=None):
     """Returns (F[n,3], U, W[6], u_i[n], W_i[n,6]) for the whole system."""
     lib = lib or load()
     pos, box, n, types, nt = _common(pos, box, types, params)
-    eps, sig, rc = _pair_tables(params, nt)
+    t = _pair_tables(params, nt)
     F = np.zeros((n, 3))
     U = np.zeros(1)
     W = np.zeros(6)
     ui = np.zeros(n)
     Wi = np.zeros((n, 6))
-    rcode = lib.oracle_forces(n, box, pos, types, nt, eps, sig, rc, F, _ptr(U), _ptr(W),
-                              _ptr(ui), _ptr(Wi))
+    rcode = lib.oracle_forces(n, box, pos, types, *t.args(), F, _ptr(U), _ptr(W), _ptr(ui),
+                              _ptr(Wi))
     if rcode:
         raise ValueError(f"oracle_forces failed ({rcode})")
     return F, float(U[0]), W, ui, Wi
@@ -126,13 +170,13 @@ def forces_subset(pos, box, types, params, idx, lib=None):
     """Per-particle (F[m,3], u[m], W[m,6]) for the particles listed in idx."""
     lib = lib or load()
     pos, box, n, types, nt = _common(pos, box, types, params)
-    eps, sig, rc = _pair_tables(params, nt)
+    t = _pair_tables(params, nt)
     idx = np.ascontiguousarray(idx, np.int64)
     m = idx.shape[0]
     F = np.zeros((m, 3))
     u = np.zeros(m)
     W = np.zeros((m, 6))
-    rcode = lib.oracle_forces_subset(n, box, pos, types, nt, eps, sig, rc, m, idx, F, _ptr(u),
+    rcode = lib.oracle_forces_subset(n, box, pos, types, *t.args(), m, idx, F, _ptr(u),
                                      _ptr(W))
     if rcode:
         raise ValueError(f"oracle_forces_subset failed ({rcode})")
@@ -196,12 +240,12 @@ def vv_run(pos, vel, box, types, params, mass, dt, nsteps, image=None, series=Fa
     pos = pos.copy()
     vel = np.array(vel, np.float64).reshape(-1, 3)
     image = np.zeros((n, 3), np.int32) if image is None else np.array(image, np.int32)
-    eps, sig, rc = _pair_tables(params, nt)
+    t = _pair_tables(params, nt)
     F = np.zeros((n, 3))
     pe = np.zeros(nsteps + 1) if series else None
     ke = np.zeros(nsteps + 1) if series else None
-    rcode = lib.oracle_vv(n, box, pos, vel, image, types, nt, eps, sig, rc, float(mass),
-                          float(dt), int(nsteps), F, _ptr(pe), _ptr(ke))
+    rcode = lib.oracle_vv(n, box, pos, vel, image, types, *t.args(), float(mass), float(dt),
+                          int(nsteps), F, _ptr(pe), _ptr(ke))
     if rcode:
         raise ValueError(f"oracle_vv failed ({rcode})")
     out = dict(pos=pos, vel=vel, image=image, force=F)
@@ -220,11 +264,11 @@ def nvt_run(pos, vel, box, types, params, mass, dt, kT, tau, nsteps, xi=0.0, eta
     pos = pos.copy()
     vel = np.array(vel, np.float64).reshape(-1, 3)
     image = np.zeros((n, 3), np.int32) if image is None else np.array(image, np.int32)
-    eps, sig, rc = _pair_tables(params, nt)
+    t = _pair_tables(params, nt)
     F = np.zeros((n, 3))
     ser = [np.zeros(nsteps + 1) if series else None for _ in range(4)]
     x, e = C.c_double(xi), C.c_double(eta)
-    rcode = lib.oracle_nvt(n, box, pos, vel, image, types, nt, eps, sig, rc, float(mass),
+    rcode = lib.oracle_nvt(n, box, pos, vel, image, types, *t.args(), float(mass),
                            float(dt), float(kT), float(tau), int(nsteps), F, C.byref(x),
                            C.byref(e), *[_ptr(a) for a in ser])
     if rcode:

@@ -20,6 +20,20 @@
  *      V(r) = 0                                                   otherwise
  *    force on i from j:  F_ij = 24 eps [2 (sigma/r)^12 - (sigma/r)^6] / r^2 * d_ij
  *    (the force is not shifted).
+ *  - the other short-range pair potentials named with LJ in Section 3.1 ("Mie,
+ *    WCA, Yukawa, Gaussian"; the paper gives no formulas, these are their
+ *    textbook forms), each truncated at r_cut and shifted by its value there,
+ *    the force not shifted (kind codes as in the C library's interface):
+ *      1 Mie(n, m):  V = C eps [(sigma/r)^n - (sigma/r)^m],
+ *                    C = n/(n-m) (n/m)^(m/(n-m))  (so min V = -eps);
+ *                    f = C eps [n (sigma/r)^n - m (sigma/r)^m] / r^2
+ *      2 WCA:        12-6 LJ cut at its minimum, r_cut = 2^(1/6) sigma whatever
+ *                    the rcut table says, so V = 4 eps [...] + eps >= 0
+ *      3 Yukawa(kappa): V = eps exp(-kappa r) / r;
+ *                    f = eps exp(-kappa r) (1 + kappa r) / r^3
+ *      4 Gaussian:   V = eps exp(-r^2 / (2 sigma^2));  f = eps / sigma^2 exp(...)
+ *    with F_ij = f d_ij as for LJ.  Mie takes n, m and Yukawa kappa from two
+ *    extra per type-pair tables (pa, pb).
  *  - totals: F_i = sum_{j != i} F_ij;  U = sum_{i<j} V(r_ij);
  *    virial tensor W_ab = sum_{i<j} d_ij,a F_ij,b, stored xx,xy,xz,yy,yz,zz;
  *    per-particle energy and virial take half of every pair they are in.
@@ -76,11 +90,78 @@ static void lj_pair(double r2, double eps, double sigma, double rc, double *v, d
     *f = 24.0 * eps * (2.0 * s12 - s6) / r2;
 }
 
+enum { POT_LJ = 0, POT_MIE = 1, POT_WCA = 2, POT_YUKAWA = 3, POT_GAUSS = 4, POT_COUNT = 5 };
+
+/* the pair interaction: which potential, and its per type-pair tables */
+typedef struct {
+    int32_t ntypes, kind;
+    const double *eps, *sigma, *rcut, *pa, *pb;
+} pair_model;
+
+/* the cut-off radius of type pair p (WCA: the LJ minimum) */
+static double cut_of(const pair_model *m, int32_t p)
+{
+    if (m->kind == POT_WCA) return pow(2.0, 1.0 / 6.0) * m->sigma[p];
+    return m->rcut[p];
+}
+
+/* unshifted Mie energy and f at squared distance r2 */
+static void mie_raw(double r2, double eps, double sigma, double n, double m, double *v, double *f)
+{
+    double c = n / (n - m) * pow(n / m, m / (n - m));
+    double sn = pow(sigma * sigma / r2, 0.5 * n); /* (sigma/r)^n */
+    double sm = pow(sigma * sigma / r2, 0.5 * m);
+    *v = c * eps * (sn - sm);
+    *f = c * eps * (n * sn - m * sm) / r2;
+}
+
+/* unshifted Yukawa energy and f at squared distance r2 */
+static void yukawa_raw(double r2, double eps, double kappa, double *v, double *f)
+{
+    double r = sqrt(r2);
+    double e = eps * exp(-kappa * r) / r;
+    *v = e;
+    *f = e * (1.0 + kappa * r) / r2;
+}
+
+/* unshifted Gaussian energy and f at squared distance r2 */
+static void gauss_raw(double r2, double eps, double sigma, double *v, double *f)
+{
+    double e = eps * exp(-r2 / (2.0 * sigma * sigma));
+    *v = e;
+    *f = e / (sigma * sigma);
+}
+
+/* The pair interaction of type pair p at squared distance r2 < rc^2: energy shifted
+ * by its value at rc, unshifted force factor f (F_ij = f d_ij). */
+static void pair_terms(const pair_model *m, int32_t p, double r2, double rc, double *v, double *f)
+{
+    double vc, fc;
+    switch (m->kind) {
+    case POT_MIE:
+        mie_raw(r2, m->eps[p], m->sigma[p], m->pa[p], m->pb[p], v, f);
+        mie_raw(rc * rc, m->eps[p], m->sigma[p], m->pa[p], m->pb[p], &vc, &fc);
+        *v -= vc;
+        break;
+    case POT_YUKAWA:
+        yukawa_raw(r2, m->eps[p], m->pa[p], v, f);
+        yukawa_raw(rc * rc, m->eps[p], m->pa[p], &vc, &fc);
+        *v -= vc;
+        break;
+    case POT_GAUSS:
+        gauss_raw(r2, m->eps[p], m->sigma[p], v, f);
+        gauss_raw(rc * rc, m->eps[p], m->sigma[p], &vc, &fc);
+        *v -= vc;
+        break;
+    default: /* LJ, and WCA with its own rc */
+        lj_pair(r2, m->eps[p], m->sigma[p], rc, v, f);
+    }
+}
+
 /* All interactions of particle i (j runs over every other particle, ascending).
  * Outputs the force on i, half of its pair energies and half of its pair virials. */
 static void particle_terms(int64_t i, int64_t n, const double *box, const double *pos,
-                           const int32_t *type, int32_t ntypes, const double *eps,
-                           const double *sigma, const double *rcut, double f_out[3],
+                           const int32_t *type, const pair_model *m, double f_out[3],
                            double *u_out, double w_out[6])
 {
     double fx = 0, fy = 0, fz = 0, u = 0;
@@ -92,11 +173,11 @@ static void particle_terms(int64_t i, int64_t n, const double *box, const double
         double dy = min_image(pos[3 * i + 1] - pos[3 * j + 1], box[1]);
         double dz = min_image(pos[3 * i + 2] - pos[3 * j + 2], box[2]);
         double r2 = dx * dx + dy * dy + dz * dz;
-        int32_t p = ti * ntypes + type[j];
-        double rc = rcut[p];
+        int32_t p = ti * m->ntypes + type[j];
+        double rc = cut_of(m, p);
         if (!(r2 < rc * rc)) continue;
         double v, f;
-        lj_pair(r2, eps[p], sigma[p], rc, &v, &f);
+        pair_terms(m, p, r2, rc, &v, &f);
         fx += f * dx;
         fy += f * dy;
         fz += f * dz;
@@ -123,6 +204,35 @@ static int check_common(int64_t n, const double *box, int32_t ntypes)
     return 0;
 }
 
+/* the pair model of the arguments, or -1 if a table its kind needs is missing */
+static int make_model(pair_model *m, int32_t ntypes, int32_t kind, const double *eps,
+                      const double *sigma, const double *rcut, const double *pa,
+                      const double *pb)
+{
+    m->ntypes = ntypes;
+    m->kind = kind;
+    m->eps = eps;
+    m->sigma = sigma;
+    m->rcut = rcut;
+    m->pa = pa;
+    m->pb = pb;
+    if (kind < 0 || kind >= POT_COUNT || !eps) return -1;
+    if (kind != POT_YUKAWA && !sigma) return -1;
+    if (kind != POT_WCA && !rcut) return -1;
+    if ((kind == POT_MIE && (!pa || !pb)) || (kind == POT_YUKAWA && !pa)) return -1;
+    return 0;
+}
+
+/* the same model with every entry's cut-off resolved (cut_of) into rc_out */
+static void resolved_cuts(const pair_model *m, double *rc_out)
+{
+    for (int32_t p = 0; p < m->ntypes * m->ntypes; ++p) rc_out[p] = cut_of(m, p);
+}
+
+static int forces_model(int64_t n, const double *box, const double *pos, const int32_t *type,
+                        const pair_model *m, double *force, double *energy, double *virial,
+                        double *per_energy, double *per_virial);
+
 /*
  * Forces, total potential energy and virial tensor of the whole system.
  * pos: n x 3 row-major, any image.  eps/sigma/rcut: ntypes x ntypes row-major.
@@ -130,11 +240,20 @@ static int check_common(int64_t n, const double *box, int32_t ntypes)
  * per_energy / per_virial: optional (NULL) per-particle halves (n, n x 6).
  */
 int oracle_forces(int64_t n, const double *box, const double *pos, const int32_t *type,
-                  int32_t ntypes, const double *eps, const double *sigma, const double *rcut,
-                  double *force, double *energy, double *virial, double *per_energy,
-                  double *per_virial)
+                  int32_t ntypes, int32_t kind, const double *eps, const double *sigma,
+                  const double *rcut, const double *pa, const double *pb, double *force,
+                  double *energy, double *virial, double *per_energy, double *per_virial)
 {
-    if (check_common(n, box, ntypes)) return -1;
+    pair_model m;
+    if (check_common(n, box, ntypes) || make_model(&m, ntypes, kind, eps, sigma, rcut, pa, pb))
+        return -1;
+    return forces_model(n, box, pos, type, &m, force, energy, virial, per_energy, per_virial);
+}
+
+static int forces_model(int64_t n, const double *box, const double *pos, const int32_t *type,
+                        const pair_model *m, double *force, double *energy, double *virial,
+                        double *per_energy, double *per_virial)
+{
     double *u = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *w = (double *)malloc(sizeof(double) * 6 * (size_t)(n > 0 ? n : 1));
     if (!u || !w) {
@@ -144,8 +263,7 @@ int oracle_forces(int64_t n, const double *box, const double *pos, const int32_t
     }
 #pragma omp parallel for schedule(dynamic, 16) num_threads(oracle_get_threads())
     for (int64_t i = 0; i < n; ++i)
-        particle_terms(i, n, box, pos, type, ntypes, eps, sigma, rcut, &force[3 * i], &u[i],
-                       &w[6 * i]);
+        particle_terms(i, n, box, pos, type, m, &force[3 * i], &u[i], &w[6 * i]);
     double U = 0, W[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t i = 0; i < n; ++i) {
         U += u[i];
@@ -166,18 +284,21 @@ int oracle_forces(int64_t n, const double *box, const double *pos, const int32_t
  * (cost O(m n)); used to check sampled outputs of systems too large for O(n^2).
  */
 int oracle_forces_subset(int64_t n, const double *box, const double *pos, const int32_t *type,
-                         int32_t ntypes, const double *eps, const double *sigma,
-                         const double *rcut, int64_t m, const int64_t *idx, double *force,
-                         double *per_energy, double *per_virial)
+                         int32_t ntypes, int32_t kind, const double *eps, const double *sigma,
+                         const double *rcut, const double *pa, const double *pb, int64_t m,
+                         const int64_t *idx, double *force, double *per_energy,
+                         double *per_virial)
 {
-    if (check_common(n, box, ntypes) || m < 0) return -1;
+    pair_model pm;
+    if (check_common(n, box, ntypes) || m < 0 ||
+        make_model(&pm, ntypes, kind, eps, sigma, rcut, pa, pb))
+        return -1;
     for (int64_t k = 0; k < m; ++k)
         if (idx[k] < 0 || idx[k] >= n) return -1;
 #pragma omp parallel for schedule(dynamic, 4) num_threads(oracle_get_threads())
     for (int64_t k = 0; k < m; ++k) {
         double u, w[6];
-        particle_terms(idx[k], n, box, pos, type, ntypes, eps, sigma, rcut, &force[3 * k], &u,
-                       w);
+        particle_terms(idx[k], n, box, pos, type, &pm, &force[3 * k], &u, w);
         if (per_energy) per_energy[k] = u;
         if (per_virial)
             for (int a = 0; a < 6; ++a) per_virial[6 * k + a] = w[a];
@@ -233,6 +354,18 @@ int oracle_neighbors(int64_t n, const double *box, const double *pos, const int3
     return 0;
 }
 
+/* The cut-off radius of every type pair (ntypes x ntypes into rc_out): the rcut
+ * table, except WCA's 2^(1/6) sigma.  Returns -1 on a missing table. */
+int oracle_cutoffs(int32_t ntypes, int32_t kind, const double *eps, const double *sigma,
+                   const double *rcut, const double *pa, const double *pb, double *rc_out)
+{
+    pair_model m;
+    if (ntypes < 1 || !rc_out || make_model(&m, ntypes, kind, eps, sigma, rcut, pa, pb))
+        return -1;
+    resolved_cuts(&m, rc_out);
+    return 0;
+}
+
 /* wrap one coordinate into [-L/2, L/2) and count the box crossings (paper silent) */
 static void wrap1(double *x, int32_t *img, double L)
 {
@@ -272,15 +405,17 @@ double oracle_kinetic(int64_t n, const double *vel, double mass)
  * taken after step s (entry 0 = initial state): pe[s], ke[s].
  */
 int oracle_vv(int64_t n, const double *box, double *pos, double *vel, int32_t *image,
-              const int32_t *type, int32_t ntypes, const double *eps, const double *sigma,
-              const double *rcut, double mass, double dt, int64_t nsteps, double *force,
-              double *pe, double *ke)
+              const int32_t *type, int32_t ntypes, int32_t kind, const double *eps,
+              const double *sigma, const double *rcut, const double *pa, const double *pb,
+              double mass, double dt, int64_t nsteps, double *force, double *pe, double *ke)
 {
-    if (check_common(n, box, ntypes) || nsteps < 0 || !(mass > 0)) return -1;
+    pair_model m;
+    if (check_common(n, box, ntypes) || nsteps < 0 || !(mass > 0) ||
+        make_model(&m, ntypes, kind, eps, sigma, rcut, pa, pb))
+        return -1;
     oracle_wrap(n, box, pos, image);
     double U;
-    int rc = oracle_forces(n, box, pos, type, ntypes, eps, sigma, rcut, force, &U, NULL, NULL,
-                           NULL);
+    int rc = forces_model(n, box, pos, type, &m, force, &U, NULL, NULL, NULL);
     if (rc) return rc;
     if (pe) pe[0] = U;
     if (ke) ke[0] = oracle_kinetic(n, vel, mass);
@@ -289,8 +424,7 @@ int oracle_vv(int64_t n, const double *box, double *pos, double *vel, int32_t *i
         for (int64_t i = 0; i < 3 * n; ++i) vel[i] += h * force[i];
         for (int64_t i = 0; i < 3 * n; ++i) pos[i] += dt * vel[i];
         oracle_wrap(n, box, pos, image);
-        rc = oracle_forces(n, box, pos, type, ntypes, eps, sigma, rcut, force, &U, NULL, NULL,
-                           NULL);
+        rc = forces_model(n, box, pos, type, &m, force, &U, NULL, NULL, NULL);
         if (rc) return rc;
         for (int64_t i = 0; i < 3 * n; ++i) vel[i] += h * force[i];
         if (pe) pe[s] = U;
@@ -313,20 +447,21 @@ int oracle_vv(int64_t n, const double *box, double *pos, double *vel, int32_t *i
  * xi_io / eta_io hold the thermostat on entry and on return; the optional series
  * (nsteps + 1 entries) record U, K, xi, eta after each step (entry 0: the start). */
 int oracle_nvt(int64_t n, const double *box, double *pos, double *vel, int32_t *image,
-               const int32_t *type, int32_t ntypes, const double *eps, const double *sigma,
-               const double *rcut, double mass, double dt, double kT, double tau,
-               int64_t nsteps, double *force, double *xi_io, double *eta_io, double *pe,
-               double *ke, double *xis, double *etas)
+               const int32_t *type, int32_t ntypes, int32_t kind, const double *eps,
+               const double *sigma, const double *rcut, const double *pa, const double *pb,
+               double mass, double dt, double kT, double tau, int64_t nsteps, double *force,
+               double *xi_io, double *eta_io, double *pe, double *ke, double *xis,
+               double *etas)
 {
+    pair_model m;
     if (check_common(n, box, ntypes) || nsteps < 0 || !(mass > 0) || !(kT > 0) || !(tau > 0) ||
-        n < 2 || !xi_io || !eta_io)
+        n < 2 || !xi_io || !eta_io || make_model(&m, ntypes, kind, eps, sigma, rcut, pa, pb))
         return -1;
     const double g = 3.0 * (double)n - 3.0;
     double xi = *xi_io, eta = *eta_io;
     oracle_wrap(n, box, pos, image);
     double U;
-    int rc = oracle_forces(n, box, pos, type, ntypes, eps, sigma, rcut, force, &U, NULL, NULL,
-                           NULL);
+    int rc = forces_model(n, box, pos, type, &m, force, &U, NULL, NULL, NULL);
     if (rc) return rc;
     if (pe) pe[0] = U;
     if (ke) ke[0] = oracle_kinetic(n, vel, mass);
@@ -342,8 +477,7 @@ int oracle_nvt(int64_t n, const double *box, double *pos, double *vel, int32_t *
         for (int64_t i = 0; i < 3 * n; ++i) vel[i] += h * force[i];
         for (int64_t i = 0; i < 3 * n; ++i) pos[i] += dt * vel[i];
         oracle_wrap(n, box, pos, image);
-        rc = oracle_forces(n, box, pos, type, ntypes, eps, sigma, rcut, force, &U, NULL, NULL,
-                           NULL);
+        rc = forces_model(n, box, pos, type, &m, force, &U, NULL, NULL, NULL);
         if (rc) return rc;
         for (int64_t i = 0; i < 3 * n; ++i) vel[i] += h * force[i];
         sc = exp(-0.5 * dt * xi);
