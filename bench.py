@@ -155,11 +155,18 @@ def make_workload(name: str, rank: int):
     if name == "plain4k":
         return wl.plain_fp64_4k(seed), "fp64", 0, \
             "lj_fluid N=4000 rho=0.84 T=1.2 rc=2.5 shifted rbuff=0.4 dt=0.005 fp64"
+    if name in POTENTIAL_WORKLOADS:   # the other pair potentials on the LJ 64k geometry
+        w = wl.potential_64k(name[:-3], seed)
+        return w, "mixed", 100, f"{name[:-3]}_fluid N=64000 rho=0.84 T=1.2 {w.meta['pair']} " \
+                                "rbuff=0.4 dt=0.005"
     if name in ("paper64k", "paper64k_mixed"):   # Section 5's LJ benchmark, NVT
         prec = "fp64" if name == "paper64k" else "mixed"
         return wl.paper_lj_64k(seed), prec, 100, \
             f"lj_fluid N=64000 rho=0.382 kT=1.2 rc=3.0 shifted rbuff=0.4 dt=0.005 NVT tau=1.0 {prec}"
     raise SystemExit(f"unknown workload {name}")
+
+
+POTENTIAL_WORKLOADS = ("mie64k", "wca64k", "yukawa64k", "gauss64k")
 
 
 def integrator_kw(w):
@@ -185,7 +192,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_force.cu", "gbmd_internal.cuh"):
+    for f in ("k_force.cuh", "k_force.cu", "step_core.cuh", "gbmd_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1308_5587_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -671,7 +678,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["gbmd", "reference"], default="gbmd")
     ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k", "paper64k", "paper64k_mixed",
-                                           "batch", "serve"],
+                                           *POTENTIAL_WORKLOADS, "batch", "serve"],
                     default="lj64k")
     ap.add_argument("--replicas", type=int, default=256, help="batch workload: replicas")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: fixed tuning")

@@ -2,6 +2,8 @@
  * gbmd.h -- C ABI of libgbmd, a GB300 (sm_103a) Lennard-Jones molecular-dynamics
  * hot path: cell list, Verlet neighbour list with skin, LJ pair force and a fused
  * velocity-Verlet NVE step, for one system or for many systems stepped together.
+ * The same gather also evaluates the other short-range pair potentials Section 3.1
+ * lists beside LJ (Mie, WCA, Yukawa, Gaussian; gbmd_desc.potential).
  *
  * The calls follow the HOOMD-blue paper's statement of the problem:
  *   - a system is particles with positions and types in a periodic box
@@ -46,7 +48,7 @@
 extern "C" {
 #endif
 
-#define GBMD_ABI_VERSION 4
+#define GBMD_ABI_VERSION 5
 #define GBMD_MAX_TYPES 4
 
 typedef enum gbmd_status {
@@ -76,9 +78,11 @@ typedef struct gbmd_desc {
     const int32_t *type;        /* n type ids in [0, ntypes); NULL = all type 0 */
     const int32_t *image;       /* n x 3 initial image counts; NULL = all 0 */
     int32_t ntypes;             /* 1 .. GBMD_MAX_TYPES */
-    const double *eps;          /* ntypes x ntypes, symmetric, > 0 */
-    const double *sigma;        /* ntypes x ntypes, symmetric, > 0 */
-    const double *rcut;         /* ntypes x ntypes, symmetric, > 0 (r_cut per pair) */
+    const double *eps;          /* ntypes x ntypes, symmetric, > 0 (finite, nonzero for
+                                   Yukawa and Gaussian) */
+    const double *sigma;        /* ntypes x ntypes, symmetric, > 0 (unread for Yukawa) */
+    const double *rcut;         /* ntypes x ntypes, symmetric, > 0 (r_cut per pair; unread
+                                   for WCA) */
     double r_buff;              /* neighbour-list skin, >= 0 */
     double dt;                  /* time step, > 0 */
     double mass;                /* particle mass, > 0 */
@@ -110,10 +114,42 @@ typedef struct gbmd_desc {
                                    Verlet, scale/2, xi/2.  NVT uses the global force path. */
     double kT;                  /* NVT target temperature (> 0) */
     double tau;                 /* NVT coupling time (> 0) */
+    int32_t potential;          /* the pair potential (gbmd_potential; 0 = LJ).  Every one
+                                   is truncated at r_cut,ij and shifted by its value there
+                                   (the force is not shifted), d_ij = x_i - x_j,
+                                   F_ij = f(r) d_ij:
+                                   GBMD_POT_LJ: the 12-6 form above.
+                                   GBMD_POT_MIE: V = C eps [(sigma/r)^n - (sigma/r)^m],
+                                     C = n/(n-m) (n/m)^(m/(n-m)) (depth -eps at the
+                                     minimum), f = C eps [n (sigma/r)^n - m (sigma/r)^m]/r^2;
+                                     n, m from mie_n, mie_m (n > m > 0, real).
+                                   GBMD_POT_WCA: the 12-6 form cut at its minimum:
+                                     r_cut,ij = 2^(1/6) sigma_ij; rcut is not read (may be
+                                     NULL); V = 4 eps [...] + eps >= 0.
+                                   GBMD_POT_YUKAWA: V = eps exp(-kappa r)/r,
+                                     f = eps exp(-kappa r) (1 + kappa r)/r^3; kappa >= 0
+                                     from `kappa`; sigma is not read (may be NULL); eps may
+                                     have either sign.
+                                   GBMD_POT_GAUSS: V = eps exp(-r^2/(2 sigma^2)),
+                                     f = eps/sigma^2 exp(-r^2/(2 sigma^2)); eps may have
+                                     either sign.
+                                   Systems stepped together in one batch share the
+                                   evaluator (LJ and WCA share one).  The staged force path
+                                   serves LJ and WCA only; the others use the global one. */
+    const double *mie_n;        /* ntypes x ntypes, symmetric (GBMD_POT_MIE; else unread) */
+    const double *mie_m;        /* ntypes x ntypes, symmetric, 0 < m < n (GBMD_POT_MIE) */
+    const double *kappa;        /* ntypes x ntypes, symmetric, >= 0 (GBMD_POT_YUKAWA) */
 } gbmd_desc;
 
 enum { GBMD_PATH_GLOBAL = 0, GBMD_PATH_STAGED = 1 };
 enum { GBMD_NVE = 0, GBMD_NVT = 1 };
+typedef enum gbmd_potential {
+    GBMD_POT_LJ = 0,
+    GBMD_POT_MIE = 1,
+    GBMD_POT_WCA = 2,
+    GBMD_POT_YUKAWA = 3,
+    GBMD_POT_GAUSS = 4
+} gbmd_potential;
 
 /* Thermodynamic quantities of one system at its current step (FP64). */
 typedef struct gbmd_thermo {

@@ -102,6 +102,7 @@ struct Group {
   size_t cap_tb = 0, cap_tbk = 0, cap_te = 0;
   int window_cap = 0;                        // largest staged window among members
   bool nvt = false;                          // the members integrate NVT (all or none)
+  int eval = EVAL_LJ;                        // the members' pair evaluator (all the same)
   double* d_nhpart = nullptr;                // NVT: per-step-tile v.v partial sums
   size_t cap_nhpart = 0;
   double* d_partials = nullptr;
@@ -165,6 +166,7 @@ int sync_layout(Group* g) {
   g->rel = true;
   g->window_cap = 0;
   g->nvt = !m.empty() && m[0]->h.nvt;
+  g->eval = m.empty() ? EVAL_LJ : m[0]->h.eval;
   for (size_t k = 0; k < m.size(); ++k) {
     SysDev d = m[k]->h;
     const int n = d.n;
@@ -267,14 +269,14 @@ std::vector<KernelCall> rebuild_calls(const Group* g) {
 // forces at the current positions, outside the step (autotuning, readouts)
 KernelCall plain_force_call(const Group* g) {
   return force_call(g->precision, g->multi, MODE_FORCE, g->tpp, g->fblock, g->d_desc, g->d_tf,
-                    g->ntf, g->d_ctl, StepArgs{});
+                    g->ntf, g->d_ctl, StepArgs{}, g->eval);
 }
 
 // energy/virial launch of the global-list systems: the step's threads per particle
 // (so the FP32 forces it writes are bitwise the step's), EV_TILE_P particles per block
 KernelCall ev_force_call(const Group* g, const SysDev* desc) {
   return force_call(g->precision, g->multi, MODE_EV, g->tpp, EV_TILE_P * g->tpp, desc, g->d_te,
-                    g->nte, g->d_ctl, StepArgs{});
+                    g->nte, g->d_ctl, StepArgs{}, g->eval);
 }
 
 // readout force launches (ev = 0 forces, 1 also energy/virial): global-list systems,
@@ -304,7 +306,7 @@ std::vector<KernelCall> step_calls(const Group* g, cudaGraphConditionalHandle co
     a.cond = 0;
     a.use_cond = 0;
     v.push_back(force_call(g->precision, g->multi, MODE_NVT_A, g->tpp, g->fblock, g->d_desc, g->d_tf,
-                           g->ntf, g->d_ctl, a));
+                           g->ntf, g->d_ctl, a, g->eval));
     StepArgs b = sa;
     b.total_blocks = g->ntp;
     v.push_back(nvt_b_call(g->precision, g->d_desc, g->d_tp, g->ntp, g->d_ctl, b));
@@ -312,7 +314,7 @@ std::vector<KernelCall> step_calls(const Group* g, cudaGraphConditionalHandle co
   }
   if (g->ntf > 0)
     v.push_back(force_call(g->precision, g->multi, MODE_STEP, g->tpp, g->fblock, g->d_desc, g->d_tf,
-                           g->ntf, g->d_ctl, sa));
+                           g->ntf, g->d_ctl, sa, g->eval));
   if (g->ntb > 0)
     v.push_back(force_staged_call(g->multi, MODE_STEP, g->d_desc, g->d_tb, g->ntb, g->d_ctl, g->nte,
                                   g->window_cap, sa));
@@ -509,12 +511,53 @@ int sync_system(gbmd_system* s) {
   return fail(GBMD_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
 }
 
+// the cut-off radius of type pair p: the rcut table, except WCA's 2^(1/6) sigma
+double cut_of(const gbmd_desc* d, int p) {
+  return d->potential == GBMD_POT_WCA ? std::pow(2.0, 1.0 / 6.0) * d->sigma[p] : d->rcut[p];
+}
+
+// the pair tables the potential reads: present, finite, in range and symmetric
+int validate_pairs(const gbmd_desc* d, double* rmax_out) {
+  const int pot = d->potential;
+  if (pot < GBMD_POT_LJ || pot > GBMD_POT_GAUSS) return fail(GBMD_ERR_BAD_ARG, "potential must be a gbmd_potential (0..4)");
+  const bool need_sigma = pot != GBMD_POT_YUKAWA, need_rcut = pot != GBMD_POT_WCA;
+  const bool signed_eps = pot == GBMD_POT_YUKAWA || pot == GBMD_POT_GAUSS;
+  if (!d->eps || (need_sigma && !d->sigma) || (need_rcut && !d->rcut))
+    return fail(GBMD_ERR_BAD_ARG, "a pair table the potential reads (eps, sigma, rcut) is NULL");
+  if (pot == GBMD_POT_MIE && (!d->mie_n || !d->mie_m)) return fail(GBMD_ERR_BAD_ARG, "Mie needs mie_n and mie_m");
+  if (pot == GBMD_POT_YUKAWA && !d->kappa) return fail(GBMD_ERR_BAD_ARG, "Yukawa needs kappa");
+  const int nt = d->ntypes;
+  double rmax = 0;
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      const int p = a * nt + b, q = b * nt + a;
+      auto sym = [&](const double* t) { return !t || t[p] == t[q]; };
+      const double e = d->eps[p];
+      if (!std::isfinite(e) || (signed_eps ? e == 0 : !(e > 0)))
+        return fail(GBMD_ERR_BAD_ARG, "eps must be finite and %s", signed_eps ? "nonzero" : "positive");
+      if (need_sigma && (!(d->sigma[p] > 0) || !std::isfinite(d->sigma[p])))
+        return fail(GBMD_ERR_BAD_ARG, "sigma must be positive and finite");
+      if (need_rcut && (!(d->rcut[p] > 0) || !std::isfinite(d->rcut[p])))
+        return fail(GBMD_ERR_BAD_ARG, "rcut must be positive and finite");
+      if (pot == GBMD_POT_MIE && !(d->mie_m[p] > 0 && d->mie_n[p] > d->mie_m[p] && std::isfinite(d->mie_n[p])))
+        return fail(GBMD_ERR_BAD_ARG, "Mie exponents need 0 < m < n (finite)");
+      if (pot == GBMD_POT_YUKAWA && !(d->kappa[p] >= 0 && std::isfinite(d->kappa[p])))
+        return fail(GBMD_ERR_BAD_ARG, "kappa must be >= 0 and finite");
+      const bool s = sym(d->eps) && (!need_sigma || sym(d->sigma)) && (!need_rcut || sym(d->rcut)) &&
+                     (pot != GBMD_POT_MIE || (sym(d->mie_n) && sym(d->mie_m))) &&
+                     (pot != GBMD_POT_YUKAWA || sym(d->kappa));
+      if (!s) return fail(GBMD_ERR_BAD_ARG, "pair parameter tables must be symmetric");
+      rmax = std::max(rmax, cut_of(d, p));
+    }
+  *rmax_out = rmax;
+  return GBMD_OK;
+}
+
 int validate(const gbmd_desc* d, bool device) {
   if (!d) return fail(GBMD_ERR_BAD_ARG, "desc is NULL");
   if (d->n < 1 || d->n > (1LL << 30)) return fail(GBMD_ERR_BAD_ARG, "n must be in [1, 2^30], got %lld", (long long)d->n);
   if (!d->pos || !d->vel) return fail(GBMD_ERR_BAD_ARG, "pos and vel must not be NULL");
   if (d->ntypes < 1 || d->ntypes > GBMD_MAX_TYPES) return fail(GBMD_ERR_BAD_ARG, "ntypes must be in [1, %d]", GBMD_MAX_TYPES);
-  if (!d->eps || !d->sigma || !d->rcut) return fail(GBMD_ERR_BAD_ARG, "eps, sigma and rcut must not be NULL");
   for (int a = 0; a < 3; ++a)
     if (!(d->box[a] > 0) || !std::isfinite(d->box[a])) return fail(GBMD_ERR_BAD_ARG, "box edges must be positive and finite");
   if (!(d->dt > 0) || !(d->mass > 0) || !(d->r_buff >= 0) || !std::isfinite(d->dt) || !std::isfinite(d->r_buff))
@@ -532,16 +575,7 @@ int validate(const gbmd_desc* d, bool device) {
     return fail(GBMD_ERR_BAD_ARG, "NVT needs kT > 0, tau > 0 and at least 2 particles");
   const int nt = d->ntypes;
   double rmax = 0;
-  for (int a = 0; a < nt; ++a)
-    for (int b = 0; b < nt; ++b) {
-      const int p = a * nt + b, q = b * nt + a;
-      if (!(d->eps[p] > 0) || !(d->sigma[p] > 0) || !(d->rcut[p] > 0) || !std::isfinite(d->eps[p]) ||
-          !std::isfinite(d->sigma[p]) || !std::isfinite(d->rcut[p]))
-        return fail(GBMD_ERR_BAD_ARG, "pair parameters must be positive and finite");
-      if (d->eps[p] != d->eps[q] || d->sigma[p] != d->sigma[q] || d->rcut[p] != d->rcut[q])
-        return fail(GBMD_ERR_BAD_ARG, "pair parameter tables must be symmetric");
-      rmax = std::max(rmax, d->rcut[p]);
-    }
+  RET(validate_pairs(d, &rmax));
   const double rl = rmax + d->r_buff;
   for (int a = 0; a < 3; ++a)
     if (d->box[a] < 2.0 * rl)
@@ -554,6 +588,50 @@ int validate(const gbmd_desc* d, bool device) {
         if (d->type[i] < 0 || d->type[i] >= nt) return fail(GBMD_ERR_BAD_ARG, "type id out of range at %lld", (long long)i);
   }
   return GBMD_OK;
+}
+
+// the evaluator coefficients of type pair p (PairD's p0..p4 and the unshifted
+// V(r_cut) as `shift`), cut at rc
+void pair_coefficients(const gbmd_desc* d, int p, double rc, PairD* c) {
+  const double e = d->eps[p];
+  switch (d->potential) {
+    case GBMD_POT_MIE: {
+      const double sg = d->sigma[p], n = d->mie_n[p], m = d->mie_m[p];
+      const double ce = n / (n - m) * std::pow(n / m, m / (n - m)) * e;
+      const double x = sg * sg / (rc * rc);
+      c->p0 = sg * sg;
+      c->p1 = 0.5 * n;
+      c->p2 = 0.5 * m;
+      c->p3 = ce;
+      c->shift = ce * (std::pow(x, 0.5 * n) - std::pow(x, 0.5 * m));
+      break;
+    }
+    case GBMD_POT_YUKAWA: {
+      const double k = d->kappa[p];
+      c->p0 = e;
+      c->p1 = k;
+      c->shift = e * std::exp(-k * rc) / rc;
+      break;
+    }
+    case GBMD_POT_GAUSS: {
+      const double sg = d->sigma[p];
+      c->p0 = e;
+      c->p1 = 1.0 / (2.0 * sg * sg);
+      c->p2 = e / (sg * sg);
+      c->shift = e * std::exp(-rc * rc / (2.0 * sg * sg));
+      break;
+    }
+    default: {   // LJ; WCA with rc = 2^(1/6) sigma
+      const double sg = d->sigma[p];
+      const double s6 = std::pow(sg, 6.0), s12 = s6 * s6;
+      const double c2 = sg * sg / (rc * rc), c6 = c2 * c2 * c2, c12 = c6 * c6;
+      c->p0 = 48.0 * e * s12;
+      c->p1 = 24.0 * e * s6;
+      c->p3 = 4.0 * e * s12;
+      c->p4 = 4.0 * e * s6;
+      c->shift = 4.0 * e * (c12 - c6);
+    }
+  }
 }
 
 struct Geometry {
@@ -574,7 +652,7 @@ Geometry geometry(const gbmd_desc* d) {
   Geometry g;
   const int nt = d->ntypes;
   double rmax = 0;
-  for (int p = 0; p < nt * nt; ++p) rmax = std::max(rmax, d->rcut[p]);
+  for (int p = 0; p < nt * nt; ++p) rmax = std::max(rmax, cut_of(d, p));
   g.rl_max = rmax + d->r_buff;
   g.ncells = 1;
   for (int a = 0; a < 3; ++a) {
@@ -721,7 +799,8 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   h.mass = d->mass;
   h.h = 0.5 * d->dt / d->mass;
   s->rl_max = geo.rl_max;
-  s->want_staged = d->force_path == GBMD_PATH_STAGED && d->integrator == GBMD_NVE;
+  s->want_staged = d->force_path == GBMD_PATH_STAGED && d->integrator == GBMD_NVE &&
+                   eval_of(d->potential) == EVAL_LJ;
   h.nvt = d->integrator == GBMD_NVT;
   h.kT = d->kT;
   h.tau = d->tau;
@@ -737,30 +816,24 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   }
   const double hb = 0.5 * d->r_buff;
   h.rbuff_half2 = (float)(hb * hb * (1.0 - 1e-5));
-  for (int a = 0; a < nt; ++a)
-    for (int b = 0; b < nt; ++b) {
-      const int p = a * nt + b;
-      const double e = d->eps[p], sg = d->sigma[p], rc = d->rcut[p];
-      const double s6 = std::pow(sg, 6.0), s12 = s6 * s6;
-      const double c2 = sg * sg / (rc * rc), c6 = c2 * c2 * c2, c12 = c6 * c6;
-      const double rl = rc + d->r_buff;
-      PairD& pd = h.pd[p];
-      pd.lj1 = 48.0 * e * s12;
-      pd.lj2 = 24.0 * e * s6;
-      pd.rc2 = rc * rc;
-      pd.rl2 = rl * rl;
-      pd.c12 = 4.0 * e * s12;
-      pd.c6 = 4.0 * e * s6;
-      pd.shift = 4.0 * e * (c12 - c6);
-      PairF& pf = h.pf[p];
-      pf.lj1 = (float)pd.lj1;
-      pf.lj2 = (float)pd.lj2;
-      pf.rc2 = (float)pd.rc2;
-      pf.c12 = (float)pd.c12;
-      pf.c6 = (float)pd.c6;
-      pf.shift = (float)pd.shift;
-      pf.rl2 = (float)pd.rl2;
-    }
+  h.eval = eval_of(d->potential);
+  for (int p = 0; p < nt * nt; ++p) {
+    const double rc = cut_of(d, p), rl = rc + d->r_buff;
+    PairD& pd = h.pd[p];
+    pd = PairD{};
+    pair_coefficients(d, p, rc, &pd);
+    pd.rc2 = rc * rc;
+    pd.rl2 = rl * rl;
+    PairF& pf = h.pf[p];
+    pf.p0 = (float)pd.p0;
+    pf.p1 = (float)pd.p1;
+    pf.p2 = (float)pd.p2;
+    pf.p3 = (float)pd.p3;
+    pf.p4 = (float)pd.p4;
+    pf.rc2 = (float)pd.rc2;
+    pf.shift = (float)pd.shift;
+    pf.rl2 = (float)pd.rl2;
+  }
   int rc = GBMD_OK;
   auto A = [&](void** p, size_t bytes) {
     if (rc == GBMD_OK) rc = dalloc(s, p, bytes);
@@ -1060,8 +1133,8 @@ std::string tune_key(const Group* g) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaGetDeviceProperties(&p, dev);
-  snprintf(buf, sizeof(buf), "%s|prec=%d|multi=%d|members=%d|log2n=%d|rho10=%d", p.name,
-           g->precision, g->multi, (int)m.size(), lg, rho10);
+  snprintf(buf, sizeof(buf), "%s|prec=%d|multi=%d|eval=%d|members=%d|log2n=%d|rho10=%d", p.name,
+           g->precision, g->multi, g->eval, (int)m.size(), lg, rho10);
   for (char* c = buf; *c; ++c)
     if (*c == ' ') *c = '_';
   return buf;
@@ -1352,8 +1425,10 @@ int gbmd_get_info(gbmd_system* s, gbmd_info* out) {
 }
 
 int64_t gbmd_footprint_bytes(const gbmd_desc* d) {
-  if (!d || d->n < 1 || d->ntypes < 1 || d->ntypes > GBMD_MAX_TYPES || !d->rcut)
+  if (!d || d->n < 1 || d->ntypes < 1 || d->ntypes > GBMD_MAX_TYPES)
     return fail(GBMD_ERR_BAD_ARG, "bad description");
+  double rmax = 0;
+  RET(validate_pairs(d, &rmax));
   for (int a = 0; a < 3; ++a)
     if (!(d->box[a] > 0)) return fail(GBMD_ERR_BAD_ARG, "bad box");
   return (int64_t)footprint_of(d, geometry(d));
@@ -1450,8 +1525,11 @@ int gbmd_batch_add(gbmd_batch* bh, gbmd_system* s, int32_t* slot) {
   RET(use_device(reinterpret_cast<Group*>(bh)->device));
   if (s->batch) return fail(GBMD_ERR_STATE, "system already in a batch");
   if (s->h.precision != b->precision) return fail(GBMD_ERR_BAD_ARG, "precision mismatch");
-  for (auto* m : live(b))
+  for (auto* m : live(b)) {
     if (m->h.nvt != s->h.nvt) return fail(GBMD_ERR_BAD_ARG, "a batch holds NVE or NVT systems, not both");
+    if (m->h.eval != s->h.eval)
+      return fail(GBMD_ERR_BAD_ARG, "a batch holds systems of one pair evaluator (LJ and WCA share one)");
+  }
   if (s->device != b->device) return fail(GBMD_ERR_BAD_ARG, "system and batch are on different devices");
   RET(sync_system(s));
   CK(cudaStreamSynchronize(b->stream));

@@ -84,10 +84,23 @@ __device__ __forceinline__ longlong2 load_flag_pair(const long long* p) {
   return r;
 }
 
-// pair coefficients: lj1 = 48 eps sigma^12, lj2 = 24 eps sigma^6 (force/r factors),
-// c12 = 4 eps sigma^12, c6 = 4 eps sigma^6, shift = V_LJ(r_cut)
-struct PairF { float lj1, lj2, rc2, pad; float c12, c6, shift, rl2; };
-struct PairD { double lj1, lj2, rc2, rl2; double c12, c6, shift, pad; };
+// Per type-pair coefficients of the pair evaluators (k_force.cuh); rc2 = r_cut^2,
+// rl2 = (r_cut + r_buff)^2, shift = the unshifted V(r_cut).  p0..p4 by evaluator:
+//   LJ (and WCA):  p0 = 48 eps sigma^12, p1 = 24 eps sigma^6 (force factors),
+//                  p3 = 4 eps sigma^12, p4 = 4 eps sigma^6 (energy)
+//   Mie:           p0 = sigma^2, p1 = n/2, p2 = m/2, p3 = C eps
+//   Yukawa:        p0 = eps, p1 = kappa
+//   Gaussian:      p0 = eps, p1 = 1/(2 sigma^2), p2 = eps/sigma^2
+// (unused entries are 0)
+struct PairF { float p0, p1, rc2, p2; float p3, p4, shift, rl2; };
+struct PairD { double p0, p1, rc2, rl2; double p3, p4, shift, p2; };
+
+// the pair evaluators of the force kernels (WCA runs the LJ one)
+enum PairEval : int { EVAL_LJ = GBMD_POT_LJ, EVAL_MIE = GBMD_POT_MIE,
+                      EVAL_YUKAWA = GBMD_POT_YUKAWA, EVAL_GAUSS = GBMD_POT_GAUSS };
+inline int eval_of(int potential) {
+  return potential == GBMD_POT_WCA ? EVAL_LJ : potential;
+}
 
 struct SysDev {
   // geometry
@@ -119,6 +132,7 @@ struct SysDev {
   int tile_first_s, tile_count_s;
   double dtq[3];           // dt * 2^32 / L: the drift in box-fraction units
   double mass;
+  int eval;                // PairEval of the system's potential
   // per type pair
   PairF pf[MAXT2];
   PairD pd[MAXT2];

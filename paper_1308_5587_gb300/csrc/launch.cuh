@@ -53,10 +53,12 @@ struct StepArgs {
   cudaGraphConditionalHandle cond = 0;   // the rebuild conditional of the step graph
   int use_cond = 0;
 };
+// eval: the PairEval of every system of the launch
 KernelCall force_call(int prec, int multi, int mode, int tpp, int block, const SysDev* d,
-                      const Tile* tiles_f, int ntiles, GroupCtl* ctl, const StepArgs& sa);
+                      const Tile* tiles_f, int ntiles, GroupCtl* ctl, const StepArgs& sa,
+                      int eval);
 // staged pair force: one kernel block per 2x2x2 cell block, window in shared memory
-// (mixed precision); part_base = first partial-sum slot of these tiles
+// (mixed precision, LJ evaluator); part_base = first partial-sum slot of these tiles
 KernelCall force_staged_call(int multi, int mode, const SysDev* d, const Tile* tiles_s, int ntiles,
                              GroupCtl* ctl, int part_base, int window_cap, const StepArgs& sa);
 KernelCall nvt_b_call(int prec, const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl,

@@ -41,13 +41,18 @@ class gbmd_desc(C.Structure):
                 ("mass", C.c_double), ("precision", C.c_int32), ("sort_period", C.c_int32),
                 ("nlist_capacity", C.c_int32), ("threads_per_particle", C.c_int32),
                 ("stream", C.c_void_p), ("device", C.c_int32), ("force_path", C.c_int32),
-                ("integrator", C.c_int32), ("kT", C.c_double), ("tau", C.c_double)]
+                ("integrator", C.c_int32), ("kT", C.c_double), ("tau", C.c_double),
+                ("potential", C.c_int32), ("mie_n", C.c_void_p), ("mie_m", C.c_void_p),
+                ("kappa", C.c_void_p)]
 
 
 GBMD_PATH_GLOBAL, GBMD_PATH_STAGED = 0, 1
 FORCE_PATHS = {"global": GBMD_PATH_GLOBAL, "staged": GBMD_PATH_STAGED}
 GBMD_NVE, GBMD_NVT = 0, 1
 INTEGRATORS = {"nve": GBMD_NVE, "nvt": GBMD_NVT}
+GBMD_POT_LJ, GBMD_POT_MIE, GBMD_POT_WCA, GBMD_POT_YUKAWA, GBMD_POT_GAUSS = range(5)
+POTENTIALS = {"lj": GBMD_POT_LJ, "mie": GBMD_POT_MIE, "wca": GBMD_POT_WCA,
+              "yukawa": GBMD_POT_YUKAWA, "gauss": GBMD_POT_GAUSS}
 
 
 class gbmd_thermo(C.Structure):
@@ -160,14 +165,20 @@ def _stream_handle(stream):
 def make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass, precision,
               sort_period=0, nlist_capacity=0, threads_per_particle=0, stream=None,
               image=None, device=False, cuda_device=-1, force_path="global", integrator="nve",
-              kT=0.0, tau=0.0):
-    """Build a gbmd_desc; returns (desc, keepalive) -- keep the second alive."""
+              kT=0.0, tau=0.0, potential="lj", mie_n=None, mie_m=None, kappa=None):
+    """Build a gbmd_desc; returns (desc, keepalive) -- keep the second alive.  Pair
+    tables are ntypes x ntypes arrays or scalars; a table the potential does not read
+    may be None (sigma for Yukawa, rcut for WCA, mie_n / mie_m / kappa elsewhere)."""
     eps = np.atleast_2d(np.asarray(eps, np.float64))
     nt = eps.shape[0]
     eps = np.ascontiguousarray(np.broadcast_to(eps, (nt, nt)))
-    sigma = np.ascontiguousarray(np.broadcast_to(np.atleast_2d(np.asarray(sigma, np.float64)), (nt, nt)))
-    rcut = np.ascontiguousarray(np.broadcast_to(np.atleast_2d(np.asarray(rcut, np.float64)), (nt, nt)))
-    keep = [eps, sigma, rcut]
+
+    def table(t):
+        if t is None:
+            return None
+        return np.ascontiguousarray(np.broadcast_to(np.atleast_2d(np.asarray(t, np.float64)), (nt, nt)))
+    sigma, rcut, mie_n, mie_m, kappa = (table(t) for t in (sigma, rcut, mie_n, mie_m, kappa))
+    keep = [eps, sigma, rcut, mie_n, mie_m, kappa]
     d = gbmd_desc()
     d.n = int(n)
     box = np.broadcast_to(np.asarray(box, np.float64), (3,))
@@ -197,6 +208,8 @@ def make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass, preci
     d.integrator = INTEGRATORS.get(integrator, integrator) if isinstance(integrator, str) else int(integrator)
     d.kT = float(kT)
     d.tau = float(tau)
+    d.potential = POTENTIALS.get(potential, potential) if isinstance(potential, str) else int(potential)
+    d.mie_n, d.mie_m, d.kappa = _ptr(mie_n), _ptr(mie_m), _ptr(kappa)
     return d, keep
 
 
@@ -376,11 +389,13 @@ class System:
     def __init__(self, pos, vel, box, types=None, eps=1.0, sigma=1.0, rcut=2.5, r_buff=0.4,
                  dt=0.005, mass=1.0, precision="mixed", sort_period=0, nlist_capacity=0,
                  threads_per_particle=0, stream=None, image=None, device=False, n=None,
-                 cuda_device=-1, force_path="global", integrator="nve", kT=0.0, tau=0.0):
+                 cuda_device=-1, force_path="global", integrator="nve", kT=0.0, tau=0.0,
+                 potential="lj", mie_n=None, mie_m=None, kappa=None):
         n = int(n if n is not None else np.asarray(pos).reshape(-1, 3).shape[0])
         desc, keep = make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass,
                                precision, sort_period, nlist_capacity, threads_per_particle,
-                               stream, image, device, cuda_device, force_path, integrator, kT, tau)
+                               stream, image, device, cuda_device, force_path, integrator, kT, tau,
+                               potential, mie_n, mie_m, kappa)
         self.n = n
         self.box = np.broadcast_to(np.asarray(box, np.float64), (3,)).copy()
         self.precision = precision
@@ -390,6 +405,8 @@ class System:
     @classmethod
     def from_workload(cls, w, precision="mixed", **kw):
         p = w.pairs
+        for k, v in p.potential_kw().items():
+            kw.setdefault(k, v)
         return cls(w.pos, w.vel, w.box, w.types, p.eps, p.sigma, p.rcut, w.r_buff, w.dt, w.mass,
                    precision, **kw)
 

@@ -30,22 +30,53 @@ BASE_SEED = 20130826
 
 @dataclass
 class PairTable:
-    """Per type-pair eps, sigma, r_cut (ntypes x ntypes, symmetric)."""
+    """Per type-pair eps, sigma, r_cut (ntypes x ntypes, symmetric), and the pair
+    potential with its extra tables (Mie exponents, Yukawa screening)."""
     eps: np.ndarray
     sigma: np.ndarray
     rcut: np.ndarray
+    potential: str = "lj"
+    mie_n: np.ndarray | None = None
+    mie_m: np.ndarray | None = None
+    kappa: np.ndarray | None = None
 
     @property
     def ntypes(self) -> int:
         return int(self.eps.shape[0])
 
+    def potential_kw(self):
+        """The potential and its extra tables as keyword arguments."""
+        return {"potential": self.potential, "mie_n": self.mie_n, "mie_m": self.mie_m,
+                "kappa": self.kappa}
+
     def as_dict(self):
-        return {"eps": self.eps, "sigma": self.sigma, "rcut": self.rcut}
+        return {"eps": self.eps, "sigma": self.sigma, "rcut": self.rcut, **self.potential_kw()}
 
 
 def lj_single(eps=1.0, sigma=1.0, rcut=2.5) -> PairTable:
     one = np.ones((1, 1))
     return PairTable(eps * one, sigma * one, rcut * one)
+
+
+def mie_single(n=10.0, m=6.0, eps=1.0, sigma=1.0, rcut=2.5) -> PairTable:
+    one = np.ones((1, 1))
+    return PairTable(eps * one, sigma * one, rcut * one, "mie", n * one, m * one)
+
+
+def wca_single(eps=1.0, sigma=1.0) -> PairTable:
+    """12-6 LJ cut at its minimum 2^(1/6) sigma (the rcut table is not read)."""
+    one = np.ones((1, 1))
+    return PairTable(eps * one, sigma * one, 2.0 ** (1.0 / 6.0) * sigma * one, "wca")
+
+
+def yukawa_single(eps=1.0, kappa=1.0, rcut=2.5) -> PairTable:
+    one = np.ones((1, 1))
+    return PairTable(eps * one, one, rcut * one, "yukawa", kappa=kappa * one)
+
+
+def gauss_single(eps=1.0, sigma=1.0, rcut=3.0) -> PairTable:
+    one = np.ones((1, 1))
+    return PairTable(eps * one, sigma * one, rcut * one, "gauss")
 
 
 def kob_andersen(rcut_over_sigma=2.5) -> PairTable:
@@ -148,6 +179,19 @@ def paper_lj_64k(seed: int = BASE_SEED) -> Workload:
     dt 0.005, NVT with tau 1.0 (Listing 1's coupling time); r_buff 0.4 (not given)."""
     w = lj_fluid(64000, 0.382, 1.2, seed, pairs=lj_single(rcut=3.0))
     w.meta.update(integrator="nvt", kT=1.2, tau=1.0)
+    return w
+
+
+def potential_64k(kind: str, seed: int = BASE_SEED) -> Workload:
+    """The LJ 64k geometry (N=64,000, rho 0.84, T 1.2, r_buff 0.4, dt 0.005) with one of
+    the other pair potentials: Mie 10-6 (r_cut 2.5), WCA, Yukawa (eps 1, kappa 1,
+    r_cut 2.5) or the Gaussian core (eps 1, sigma 1, r_cut 3.0)."""
+    pairs = {"mie": (mie_single(10.0, 6.0), "n=10 m=6 rc=2.5"),
+             "wca": (wca_single(), "rc=2^(1/6)"),
+             "yukawa": (yukawa_single(1.0, 1.0, 2.5), "eps=1 kappa=1 rc=2.5"),
+             "gauss": (gauss_single(1.0, 1.0, 3.0), "eps=1 sigma=1 rc=3.0")}[kind]
+    w = lj_fluid(64000, 0.84, 1.2, seed, pairs=pairs[0])
+    w.meta["pair"] = pairs[1]
     return w
 
 

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.gbmd_abi_version() == 4
+    assert lib.gbmd_abi_version() == 5
 
 
 def _desc(lib, **over):
@@ -49,7 +49,8 @@ def _desc(lib, **over):
     pos = over.pop("pos", np.zeros((n, 3)))
     vel = np.zeros((n, 3))
     kw = dict(box=over.pop("box", 20.0), types=over.pop("types", None), eps=over.pop("eps", 1.0),
-              sigma=1.0, rcut=over.pop("rcut", 2.5), r_buff=0.4, dt=over.pop("dt", 0.005),
+              sigma=over.pop("sigma", 1.0), rcut=over.pop("rcut", 2.5), r_buff=0.4,
+              dt=over.pop("dt", 0.005),
               mass=1.0, precision=over.pop("precision", "mixed"))
     return lib.make_desc(n, kw["box"], pos, vel, kw["types"], kw["eps"], kw["sigma"], kw["rcut"],
                          kw["r_buff"], kw["dt"], kw["mass"], kw["precision"], **over)
@@ -70,6 +71,20 @@ def _desc(lib, **over):
     (dict(integrator=1, kT=1.0, tau=-1.0), "BAD_ARG"),
     (dict(integrator=2), "BAD_ARG"),
     (dict(eps=np.array([[1.0, 2.0], [1.5, 1.0]])), "BAD_ARG"),     # not symmetric
+    (dict(potential=5), "BAD_ARG"),
+    (dict(potential="mie"), "BAD_ARG"),                               # no exponents
+    (dict(potential="mie", mie_n=6.0, mie_m=6.0), "BAD_ARG"),         # needs n > m
+    (dict(potential="mie", mie_n=12.0, mie_m=0.0), "BAD_ARG"),
+    (dict(potential="yukawa"), "BAD_ARG"),                            # no kappa
+    (dict(potential="yukawa", kappa=-1.0), "BAD_ARG"),
+    (dict(potential="yukawa", kappa=1.0, eps=0.0), "BAD_ARG"),
+    (dict(potential="yukawa", kappa=np.array([[1.0, 2.0], [1.0, 1.0]]),
+          eps=np.ones((2, 2))), "BAD_ARG"),                           # kappa not symmetric
+    (dict(potential="gauss", sigma=None), "BAD_ARG"),
+    (dict(potential="wca", sigma=None, rcut=None), "BAD_ARG"),
+    (dict(potential="lj", rcut=None), "BAD_ARG"),
+    (dict(potential="mie", mie_n=12.0, mie_m=6.0, eps=-1.0), "BAD_ARG"),
+    (dict(potential="wca", rcut=None, box=3.0), "BOX_TOO_SMALL"),     # 2 (2^(1/6) + 0.4) > 3
 ])
 def test_create_rejects_bad_arguments_on_the_host(lib, bad, status):
     d, keep = _desc(lib, **bad)
@@ -95,3 +110,13 @@ def test_footprint_is_host_side_and_monotone(lib):
     assert 0 < fa < fb
     # about 0.7-1.2 KB per particle for the default capacity at liquid density
     assert 300 < fb / 8000 < 3000
+
+
+def test_footprint_follows_the_potential_cut(lib):
+    """WCA reads no rcut table: its cut is 2^(1/6) sigma, so its list is shorter."""
+    lj, k1 = _desc(lib, n=8000, box=24.0)
+    wca, k2 = _desc(lib, n=8000, box=24.0, potential="wca", rcut=None)
+    yuk, k3 = _desc(lib, n=8000, box=24.0, potential="yukawa", sigma=None, kappa=1.0)
+    f_lj, f_wca = lib.gbmd_footprint_bytes(lj), lib.gbmd_footprint_bytes(wca)
+    assert 0 < f_wca < f_lj
+    assert lib.gbmd_footprint_bytes(yuk) == f_lj   # same r_cut, same layout
