@@ -155,6 +155,13 @@ def make_workload(name: str, rank: int):
     if name == "plain4k":
         return wl.plain_fp64_4k(seed), "fp64", 0, \
             "lj_fluid N=4000 rho=0.84 T=1.2 rc=2.5 shifted rbuff=0.4 dt=0.005 fp64"
+    if name in ("colloid250k", "colloid250k_cell"):   # size-disperse: the tree list's case
+        w = wl.colloid_mixture(250000, ratio=5.0, seed=seed)
+        nl = "cell" if name.endswith("_cell") else "tree"
+        w.meta["nlist"] = nl
+        return w, "mixed", 100, \
+            (f"wca_colloid_mixture N={w.n} (250000 d=1 + {w.meta['n_large']} d=5) phi=0.2+0.2 "
+             f"T=1.0 rc=2^(1/6)sigma_ij rbuff=0.4 dt=0.002 nlist={nl}")
     if name in POTENTIAL_WORKLOADS:   # the other pair potentials on the LJ 64k geometry
         w = wl.potential_64k(name[:-3], seed)
         return w, "mixed", 100, f"{name[:-3]}_fluid N=64000 rho=0.84 T=1.2 {w.meta['pair']} " \
@@ -169,12 +176,16 @@ def make_workload(name: str, rank: int):
 POTENTIAL_WORKLOADS = ("mie64k", "wca64k", "yukawa64k", "gauss64k")
 
 
-def integrator_kw(w):
-    """integrator arguments of a workload (NVE unless its meta asks for NVT)"""
+def system_kw(w):
+    """system arguments a workload asks for in its meta: the integrator (NVE unless
+    NVT) and the neighbour-list builder (cell list unless the tree)"""
     m = w.meta or {}
+    kw = {}
     if m.get("integrator") == "nvt":
-        return {"integrator": "nvt", "kT": m["kT"], "tau": m["tau"]}
-    return {}
+        kw.update(integrator="nvt", kT=m["kT"], tau=m["tau"])
+    if m.get("nlist"):
+        kw["nlist"] = m["nlist"]
+    return kw
 
 
 # Section 5: HOOMD-blue v2.6 on one V100, full FP64, this LJ workload (context only)
@@ -261,7 +272,7 @@ def e2e_loop(torch, w, precision, sort_period, stream, dev, chunk: int, iters: i
     from paper_1308_5587_gb300 import gbmd
     n = w.n
     s = gbmd.System.from_workload(w, precision=precision, sort_period=sort_period,
-                                  stream=stream, cuda_device=dev, **integrator_kw(w))
+                                  stream=stream, cuda_device=dev, **system_kw(w))
     pos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     vel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     img = torch.empty((n, 3), dtype=torch.int32, pin_memory=True).numpy()
@@ -350,7 +361,7 @@ def gpu_arm(args):
 
     s = gbmd.System.from_workload(w, precision=precision, sort_period=sort_period,
                                   stream=stream.cuda_stream, cuda_device=local,
-                                  force_path=args.force_path, **integrator_kw(w))
+                                  force_path=args.force_path, **system_kw(w))
     if args.autotune:
         s.autotune(os.path.join(ROOT, "_work", "tune_cache.txt") if os.path.isdir(
             os.path.join(ROOT, "_work")) else None)
@@ -678,7 +689,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["gbmd", "reference"], default="gbmd")
     ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k", "paper64k", "paper64k_mixed",
-                                           *POTENTIAL_WORKLOADS, "batch", "serve"],
+                                           *POTENTIAL_WORKLOADS, "colloid250k", "colloid250k_cell",
+                                           "batch", "serve"],
                     default="lj64k")
     ap.add_argument("--replicas", type=int, default=256, help="batch workload: replicas")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: fixed tuning")

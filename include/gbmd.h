@@ -139,10 +139,22 @@ typedef struct gbmd_desc {
     const double *mie_n;        /* ntypes x ntypes, symmetric (GBMD_POT_MIE; else unread) */
     const double *mie_m;        /* ntypes x ntypes, symmetric, 0 < m < n (GBMD_POT_MIE) */
     const double *kappa;        /* ntypes x ntypes, symmetric, >= 0 (GBMD_POT_YUKAWA) */
+    int32_t nlist;              /* how the neighbour list is built (the list itself, every
+                                   pair with r < r_cut,ij + r_buff, is the same):
+                                   GBMD_NLIST_CELL (0, default): cell list of width
+                                   >= r_list,max, 27-cell stencil (Listing 1's
+                                   md.nlist.cell).
+                                   GBMD_NLIST_TREE (1): a bounding volume hierarchy per
+                                   particle type, each particle querying every type's
+                                   tree with its own r_list,ij (Section 5: nlist.tree,
+                                   for size-disperse systems, where cells sized to the
+                                   largest particles hold many small ones).  Uses the
+                                   global force path. */
 } gbmd_desc;
 
 enum { GBMD_PATH_GLOBAL = 0, GBMD_PATH_STAGED = 1 };
 enum { GBMD_NVE = 0, GBMD_NVT = 1 };
+enum { GBMD_NLIST_CELL = 0, GBMD_NLIST_TREE = 1 };
 typedef enum gbmd_potential {
     GBMD_POT_LJ = 0,
     GBMD_POT_MIE = 1,
@@ -186,7 +198,9 @@ typedef struct gbmd_info {
                                      cell blocks with their 4x4x4-cell neighbourhood in
                                      shared memory, 16-bit window-local indices) */
     int32_t max_window;           /* largest staged window at the last build (particles) */
-    double cell_scale;            /* cells are at least cell_scale * r_list,max wide */
+    double cell_scale;            /* cells are at least cell_scale * r_list,max wide (tree
+                                     list: r_list,min; its cells only order the particles) */
+    int32_t nlist;                /* GBMD_NLIST_CELL or GBMD_NLIST_TREE */
 } gbmd_info;
 
 typedef struct gbmd_system gbmd_system;

@@ -72,8 +72,9 @@ struct gbmd_system {
   int batch_slot = -1;
   long long target_step = 0;  // steps requested so far (absolute), host bookkeeping
   long long step_limit = -1;
-  double rl_max = 0;          // largest r_list: the smallest allowed cell width
-  double cell_scale = 1.0;    // cell width >= cell_scale * rl_max (autotuned)
+  double cell_min = 0;        // smallest allowed cell width: r_list,max (cell list) or
+                              // r_list,min (tree list, whose cells only order particles)
+  double cell_scale = 1.0;    // cell width >= cell_scale * cell_min (autotuned)
   bool want_staged = false;   // GBMD_PATH_STAGED requested
   // staging for import/export (device)
   double *d_pos = nullptr, *d_vel = nullptr, *d_frc = nullptr;
@@ -97,9 +98,11 @@ struct Group {
   Tile *d_tb = nullptr, *d_tbk = nullptr;   // staged force blocks; their window kernel
   Tile* d_te = nullptr;   // energy/virial launches: EV_TILE_P particles per tile, whatever
                           // the tuning, so the FP64 sums do not depend on it
-  int ntp = 0, ntf = 0, ntc = 0, nts = 0, ntb = 0, ntbk = 0, nte = 0;
+  Tile* d_tt = nullptr;   // tree-list systems: tiles over their trees' leaves
+  int ntp = 0, ntf = 0, ntc = 0, nts = 0, ntb = 0, ntbk = 0, nte = 0, ntt = 0;
   size_t cap_desc = 0, cap_tp = 0, cap_tf = 0, cap_tc = 0, cap_ts = 0, cap_part = 0;
-  size_t cap_tb = 0, cap_tbk = 0, cap_te = 0;
+  size_t cap_tb = 0, cap_tbk = 0, cap_te = 0, cap_tt = 0;
+  bool any_cell = true;   // some member builds its list from cells
   int window_cap = 0;                        // largest staged window among members
   bool nvt = false;                          // the members integrate NVT (all or none)
   int eval = EVAL_LJ;                        // the members' pair evaluator (all the same)
@@ -160,13 +163,14 @@ int sync_layout(Group* g) {
   if (!g->layout_dirty) return GBMD_OK;
   std::vector<gbmd_system*> m = live(g);
   std::vector<SysDev> desc;
-  std::vector<Tile> tp, tf, tc, ts, tb, tbk, te;
+  std::vector<Tile> tp, tf, tc, ts, tb, tbk, te, tt;
   const int per_f = g->fblock / g->tpp;
   g->multi = 0;
   g->rel = true;
   g->window_cap = 0;
   g->nvt = !m.empty() && m[0]->h.nvt;
   g->eval = m.empty() ? EVAL_LJ : m[0]->h.eval;
+  g->any_cell = false;
   for (size_t k = 0; k < m.size(); ++k) {
     SysDev d = m[k]->h;
     const int n = d.n;
@@ -185,12 +189,18 @@ int sync_layout(Group* g) {
       for (int f = 0; f < n; f += EV_TILE_P) te.push_back({(int)k, f, std::min(EV_TILE_P, n - f), 0});
       d.tile_count_f = (int)te.size() - d.tile_first_f;
     }
-    for (int c = 0; c < d.ncells; c += CELLS_PER_TILE)
-      tc.push_back({(int)k, c, std::min(CELLS_PER_TILE, d.ncells - c), 0});
+    for (int c = 0; c < d.nbins; c += CELLS_PER_TILE)
+      tc.push_back({(int)k, c, std::min(CELLS_PER_TILE, d.nbins - c), 0});
     ts.push_back({(int)k, 0, 0, 0});
+    if (d.tree)
+      for (int f = 0; f < d.tree_leaves_total; f += TILE_P)
+        tt.push_back({(int)k, f, std::min(TILE_P, d.tree_leaves_total - f), 0});
     desc.push_back(d);
     if (d.ntypes > 1) g->multi = std::max(g->multi, d.ntypes > 2 ? 2 : 1);
-    if (d.nc[0] < 3 || d.nc[1] < 3 || d.nc[2] < 3) g->rel = false;
+    if (!d.tree) {
+      g->any_cell = true;
+      if (d.nc[0] < 3 || d.nc[1] < 3 || d.nc[2] < 3) g->rel = false;
+    }
   }
   for (auto& d : desc)
     if (d.staged) d.tile_first_f += (int)te.size();   // staged partial sums follow the global ones
@@ -208,6 +218,7 @@ int sync_layout(Group* g) {
   RET(grow(&g->d_tb, &g->cap_tb, tb.size()));
   RET(grow(&g->d_tbk, &g->cap_tbk, tbk.size()));
   RET(grow(&g->d_te, &g->cap_te, te.size()));
+  RET(grow(&g->d_tt, &g->cap_tt, tt.size()));
   if (!g->d_ctl) {
     CK(cudaMalloc(&g->d_ctl, sizeof(GroupCtl)));
     CK(cudaMemsetAsync(g->d_ctl, 0, sizeof(GroupCtl), g->stream));
@@ -224,6 +235,7 @@ int sync_layout(Group* g) {
   CK(up(g->d_tb, tb));
   CK(up(g->d_tbk, tbk));
   CK(up(g->d_te, te));
+  CK(up(g->d_tt, tt));
   CK(cudaStreamSynchronize(g->stream));   // host vectors die here
   g->ntp = (int)tp.size();
   g->ntf = (int)tf.size();
@@ -232,6 +244,7 @@ int sync_layout(Group* g) {
   g->ntb = (int)tb.size();
   g->ntbk = (int)tbk.size();
   g->nte = (int)te.size();
+  g->ntt = (int)tt.size();
   g->layout_dirty = false;
   destroy_graphs(g);
   return GBMD_OK;
@@ -247,23 +260,23 @@ int refresh_desc(gbmd_system* s) {
   return GBMD_OK;
 }
 
+// the rebuild: cell sort (and re-sort), then the lists -- cell-list members by
+// k_nlist (after the staged windows, if any), tree-list members by k_tree_*
 std::vector<KernelCall> rebuild_calls(const Group* g) {
-  if (g->ntbk == 0)
-    return {bin_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
-            scan_call(g->d_desc, g->d_ts, g->nts, g->d_ctl),
-            scatter_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
-            cellsort_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl),
-            permute_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
-            copyback_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
-            nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi, g->ntbk > 0)};
-  return {bin_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
-          scan_call(g->d_desc, g->d_ts, g->nts, g->d_ctl),
-          scatter_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
-          cellsort_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl),
-          permute_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
-          copyback_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
-          blocks_call(g->d_desc, g->d_tbk, g->ntbk, g->d_ctl),
-          nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi, g->ntbk > 0)};
+  std::vector<KernelCall> v = {bin_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+                               scan_call(g->d_desc, g->d_ts, g->nts, g->d_ctl),
+                               scatter_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+                               cellsort_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl),
+                               permute_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl),
+                               copyback_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl)};
+  if (g->ntbk > 0) v.push_back(blocks_call(g->d_desc, g->d_tbk, g->ntbk, g->d_ctl));
+  if (g->any_cell)
+    v.push_back(nlist_call(g->d_desc, g->d_tc, g->ntc, g->d_ctl, g->rel, g->multi, g->ntbk > 0));
+  if (g->ntt > 0) {
+    v.push_back(tree_build_call(g->d_desc, g->d_tt, g->ntt, g->d_ctl));
+    v.push_back(tree_nlist_call(g->d_desc, g->d_tp, g->ntp, g->d_ctl));
+  }
+  return v;
 }
 
 // forces at the current positions, outside the step (autotuning, readouts)
@@ -499,6 +512,8 @@ int sync_system(gbmd_system* s) {
       RET(rebuild_and_force(s, 0));   // finishes the interrupted step
       continue;
     }
+    if (f.error == DEV_TREE)
+      return fail(GBMD_ERR_TIMEOUT, "a tree traversal passed its node bound (step %lld)", f.step);
     if (f.error) return fail(GBMD_ERR_CUDA, "unknown device error %d", f.error);
     long long want = s->target_step;
     if (s->step_limit >= 0) want = std::min(want, s->step_limit);
@@ -570,6 +585,8 @@ int validate(const gbmd_desc* d, bool device) {
     return fail(GBMD_ERR_BAD_ARG, "force_path must be GBMD_PATH_GLOBAL or GBMD_PATH_STAGED");
   if (d->integrator != GBMD_NVE && d->integrator != GBMD_NVT)
     return fail(GBMD_ERR_BAD_ARG, "integrator must be GBMD_NVE or GBMD_NVT");
+  if (d->nlist != GBMD_NLIST_CELL && d->nlist != GBMD_NLIST_TREE)
+    return fail(GBMD_ERR_BAD_ARG, "nlist must be GBMD_NLIST_CELL or GBMD_NLIST_TREE");
   if (d->integrator == GBMD_NVT &&
       (!(d->kT > 0) || !(d->tau > 0) || !std::isfinite(d->kT) || !std::isfinite(d->tau) || d->n < 2))
     return fail(GBMD_ERR_BAD_ARG, "NVT needs kT > 0, tau > 0 and at least 2 particles");
@@ -637,33 +654,59 @@ void pair_coefficients(const gbmd_desc* d, int p, double rc, PairD* c) {
 struct Geometry {
   int nc[3];
   int ncells;
+  int nbins;        // sort bins: ncells, or ntypes * ncells on the tree list
   int cap;
   double rl_max;
+  double cell_min;  // smallest cell width
 };
 
-// cells per axis: as many as fit with a width of at least scale * r_list,max (the
-// 27-cell stencil then holds every neighbour), at most 1024
-int cells_along(double L, double rl_max, double scale) {
-  const int c = (int)std::floor(L / (rl_max * scale * (1.0 + 1e-6)));
+// cells per axis: as many as fit with a width of at least scale * cell_min (for the
+// cell list cell_min = r_list,max: the 27-cell stencil then holds every neighbour),
+// at most 1024
+int cells_along(double L, double cell_min, double scale) {
+  const int c = (int)std::floor(L / (cell_min * scale * (1.0 + 1e-6)));
   return std::min(std::max(c, 1), 1024);
 }
 
-Geometry geometry(const gbmd_desc* d) {
+// type_counts (particles per type, or NULL when unknown) refines the default list
+// capacity of the tree list: sum over types t of rho_t (4/3) pi r_list(i, t)^3 for the
+// worst type i, instead of rho (4/3) pi r_list,max^3
+Geometry geometry(const gbmd_desc* d, const int64_t* type_counts = nullptr) {
   Geometry g;
   const int nt = d->ntypes;
-  double rmax = 0;
-  for (int p = 0; p < nt * nt; ++p) rmax = std::max(rmax, cut_of(d, p));
+  const bool tree = d->nlist == GBMD_NLIST_TREE;
+  double rmax = 0, rmin = 1e300;
+  for (int p = 0; p < nt * nt; ++p) {
+    rmax = std::max(rmax, cut_of(d, p));
+    rmin = std::min(rmin, cut_of(d, p));
+  }
+  const double vol = d->box[0] * d->box[1] * d->box[2];
   g.rl_max = rmax + d->r_buff;
+  // the tree list's cells only order the particles: as fine as the smallest r_list,
+  // but not much finer than two particles per cell
+  g.cell_min = tree ? std::max(rmin + d->r_buff, std::cbrt(2.0 * vol / (double)d->n)) : g.rl_max;
   g.ncells = 1;
   for (int a = 0; a < 3; ++a) {
-    g.nc[a] = cells_along(d->box[a], g.rl_max, 1.0);
+    g.nc[a] = cells_along(d->box[a], g.cell_min, 1.0);
     g.ncells *= g.nc[a];
   }
+  g.nbins = tree ? nt * g.ncells : g.ncells;
   if (d->nlist_capacity > 0) {
     g.cap = (int)round_up((size_t)d->nlist_capacity, 4);   // whole slot groups
   } else {
-    const double rho = (double)d->n / (d->box[0] * d->box[1] * d->box[2]);
-    const double nexp = rho * 4.0 / 3.0 * M_PI * g.rl_max * g.rl_max * g.rl_max;
+    const double rho = (double)d->n / vol;
+    double nexp = rho * 4.0 / 3.0 * M_PI * g.rl_max * g.rl_max * g.rl_max;
+    if (tree && type_counts) {
+      nexp = 0;
+      for (int a = 0; a < nt; ++a) {
+        double e = 0;
+        for (int b = 0; b < nt; ++b) {
+          const double rl = cut_of(d, a * nt + b) + d->r_buff;
+          e += (double)type_counts[b] / vol * 4.0 / 3.0 * M_PI * rl * rl * rl;
+        }
+        if (type_counts[a] > 0) nexp = std::max(nexp, e);
+      }
+    }
     g.cap = (int)round_up((size_t)(nexp * 1.4 + 24), 8);
     g.cap = std::min<int>(g.cap, (int)std::max<int64_t>(8, round_up((size_t)d->n, 8)));
   }
@@ -688,7 +731,9 @@ size_t footprint_of(const gbmd_desc* d, const Geometry& g) {
   if (d->precision == GBMD_FP64) b += n * 32 * 2;   // p64 (two buffers)
   b += n * (d->precision == GBMD_FP64 ? 32 : 16);   // force
   b += n * 4 + round_up(n, 32) * 4 * (size_t)g.cap;  // nn, nl (ELL4)
-  b += n * 4 * 4 + (size_t)(g.ncells + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;  // cells
+  b += n * 4 * 4 + (size_t)(g.nbins + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;   // cells
+  if (d->nlist == GBMD_NLIST_TREE)   // tree boxes and arrival counters (<= n + 4 ntypes nodes)
+    b += (n + 4 * (size_t)d->ntypes) * (sizeof(TreeBox) + 4);
   b += (size_t)((g.nc[0] + 1) / 2) * ((g.nc[1] + 1) / 2) * ((g.nc[2] + 1) / 2) *
        (WIN_CELLS * 8 + 16);                                                      // staged blocks
   b += n * (8 * 3 * 2 + 4 * 3 + 4 * 2 + 16);         // re-sort scratch
@@ -721,9 +766,9 @@ int setup_cells(gbmd_system* s, const int nc[3], cudaStream_t st) {
   SysDev& h = s->h;
   CK(cudaStreamSynchronize(st));
   if (h.cell_cnt) {
-    const size_t oc = (size_t)h.ncells, ob = (size_t)h.nblocks;
-    dfree(s, h.cell_cnt, (oc + 1) * 4); dfree(s, h.cell_start, (oc + 1) * 4);
-    dfree(s, h.cell_cursor, (oc + 1) * 4);
+    const size_t oc = (size_t)h.ncells, ob = (size_t)h.nblocks, obins = (size_t)h.nbins;
+    dfree(s, h.cell_cnt, (obins + 1) * 4); dfree(s, h.cell_start, (obins + 1) * 4);
+    dfree(s, h.cell_cursor, (obins + 1) * 4);
     dfree(s, const_cast<int*>(h.rank2lin), oc * 4); dfree(s, const_cast<int*>(h.lin2rank), oc * 4);
     dfree(s, h.blk_win, ob * WIN_CELLS * sizeof(int2)); dfree(s, h.blk_info, ob * sizeof(int4));
     h.cell_cnt = h.cell_start = h.cell_cursor = nullptr;
@@ -740,14 +785,16 @@ int setup_cells(gbmd_system* s, const int nc[3], cudaStream_t st) {
   }
   h.ncells = ncells;
   h.nblocks = nblocks;
+  h.nbins = h.tree ? h.ntypes * ncells : ncells;   // the tree list sorts type-major
+  const size_t nbins = (size_t)h.nbins;
   int rc = GBMD_OK;
   auto A = [&](void** p, size_t bytes) {
     if (rc == GBMD_OK) rc = dalloc(s, p, bytes);
   };
   A((void**)&h.blk_win, (size_t)nblocks * WIN_CELLS * sizeof(int2));
   A((void**)&h.blk_info, (size_t)nblocks * sizeof(int4));
-  A((void**)&h.cell_cnt, ((size_t)ncells + 1) * 4); A((void**)&h.cell_start, ((size_t)ncells + 1) * 4);
-  A((void**)&h.cell_cursor, ((size_t)ncells + 1) * 4);
+  A((void**)&h.cell_cnt, (nbins + 1) * 4); A((void**)&h.cell_start, (nbins + 1) * 4);
+  A((void**)&h.cell_cursor, (nbins + 1) * 4);
   int *r2l = nullptr, *l2r = nullptr;
   A((void**)&r2l, (size_t)ncells * 4); A((void**)&l2r, (size_t)ncells * 4);
   h.rank2lin = r2l;
@@ -768,7 +815,7 @@ int setup_cells(gbmd_system* s, const int nc[3], cudaStream_t st) {
   }
   CK(cudaMemcpyAsync(r2l, rl.data(), (size_t)ncells * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(l2r, lr.data(), (size_t)ncells * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(h.cell_cnt, 0, ((size_t)ncells + 1) * 4, st));
+  CK(cudaMemsetAsync(h.cell_cnt, 0, (nbins + 1) * 4, st));
   CK(cudaStreamSynchronize(st));   // the host tables die here
   return GBMD_OK;
 }
@@ -783,7 +830,23 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   if (dev < 0) CK(cudaGetDevice(&dev));
   if (dev >= ndev) return fail(GBMD_ERR_BAD_ARG, "device %d does not exist (%d devices)", dev, ndev);
   RET(use_device(dev));
-  const Geometry geo = geometry(d);
+  const bool tree = d->nlist == GBMD_NLIST_TREE;
+  int64_t tcount[GBMD_MAX_TYPES] = {0, 0, 0, 0};   // particles per type (tree list)
+  if (tree) {
+    std::vector<int32_t> ty;
+    const int32_t* tp = d->type;
+    if (tp && device) {   // the tree layout is fixed by the type counts: read them once
+      ty.resize((size_t)d->n);
+      CK(cudaMemcpy(ty.data(), tp, (size_t)d->n * 4, cudaMemcpyDeviceToHost));
+      tp = ty.data();
+    }
+    for (int64_t i = 0; i < d->n; ++i) {
+      const int t = tp ? tp[i] : 0;
+      if (t < 0 || t >= d->ntypes) return fail(GBMD_ERR_BAD_ARG, "type id out of range at %lld", (long long)i);
+      ++tcount[t];
+    }
+  }
+  const Geometry geo = geometry(d, tree ? tcount : nullptr);
   gbmd_system* s = new gbmd_system();
   s->device = dev;
   s->stream = (cudaStream_t)d->stream;
@@ -798,9 +861,25 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   h.dt = d->dt;
   h.mass = d->mass;
   h.h = 0.5 * d->dt / d->mass;
-  s->rl_max = geo.rl_max;
+  s->cell_min = geo.cell_min;
   s->want_staged = d->force_path == GBMD_PATH_STAGED && d->integrator == GBMD_NVE &&
-                   eval_of(d->potential) == EVAL_LJ;
+                   eval_of(d->potential) == EVAL_LJ && !tree;
+  h.tree = tree ? 1 : 0;
+  int nodes = 0;
+  if (tree) {   // type t: particles [first, first + n) of the sorted order, P leaves
+    int first = 0, leaves = 0;
+    for (int t = 0; t < nt; ++t) {
+      h.tree_first[t] = first;
+      h.tree_n[t] = (int)tcount[t];
+      h.tree_P[t] = tree_leaves((int)tcount[t]);
+      h.tree_leaf0[t] = leaves;
+      h.tree_node0[t] = nodes;
+      first += (int)tcount[t];
+      leaves += h.tree_P[t];
+      nodes += 2 * h.tree_P[t];   // boxes 1 .. 2P - 1 (0 unused)
+    }
+    h.tree_leaves_total = leaves;
+  }
   h.nvt = d->integrator == GBMD_NVT;
   h.kT = d->kT;
   h.tau = d->tau;
@@ -853,6 +932,10 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   A((void**)&h.type_alt, N * 4); A((void**)&h.tag_alt, N * 4); A((void**)&h.q_alt, N * 16);
   A((void**)&h.thermo, 16 * 8);
   A((void**)&h.nh, 4 * 8);
+  if (tree) {
+    A((void**)&h.tree_box, (size_t)nodes * sizeof(TreeBox));
+    A((void**)&h.tree_arrive, (size_t)nodes * 4);
+  }
   A((void**)&s->d_flags, sizeof(Flags));
   A((void**)&s->d_pos, N * 24); A((void**)&s->d_vel, N * 24); A((void**)&s->d_frc, N * 24);
   A((void**)&s->d_img, N * 12); A((void**)&s->d_type, N * 4); A((void**)&s->d_misc, 64);
@@ -866,6 +949,7 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
     const double nh0[4] = {0.0, 0.0, 1.0, 0.0};   // xi, eta, exp(-xi dt/2)
     cudaError_t e5 = cudaMemsetAsync(s->d_flags, 0, sizeof(Flags), st);
     cudaError_t e6 = cudaMemsetAsync(h.nn, 0, N * 4, st);
+    if (tree && e6 == cudaSuccess) e6 = cudaMemsetAsync(h.tree_arrive, 0, (size_t)nodes * 4, st);
     cudaError_t e7 = cudaMemcpyAsync(h.nh, nh0, sizeof(nh0), cudaMemcpyHostToDevice, st);
     cudaError_t e4 = cudaStreamSynchronize(st);
     if (e7) { gbmd_destroy(s); return fail(GBMD_ERR_CUDA, "thermostat upload failed"); }
@@ -1048,7 +1132,7 @@ int regrid(gbmd_system* s, double scale) {
   if (!(scale >= 1.0 && scale <= 4.0)) return fail(GBMD_ERR_BAD_ARG, "cell scale must be in [1, 4]");
   SysDev& h = s->h;
   int nc[3];
-  for (int a = 0; a < 3; ++a) nc[a] = cells_along(h.L[a], s->rl_max, scale);
+  for (int a = 0; a < 3; ++a) nc[a] = cells_along(h.L[a], s->cell_min, scale);
   s->cell_scale = scale;
   if (nc[0] == h.nc[0] && nc[1] == h.nc[1] && nc[2] == h.nc[2]) return GBMD_OK;
   RET(sync_system(s));   // nothing in flight, nothing owed
@@ -1187,7 +1271,7 @@ int autotune_group(Group* g, const char* cache) {
       for (double sc : {1.0, 1.1, 1.2, 1.35}) {
         std::vector<int> grid;
         for (auto* s : live(g))
-          for (int a = 0; a < 3; ++a) grid.push_back(cells_along(s->h.L[a], s->rl_max, sc));
+          for (int a = 0; a < 3; ++a) grid.push_back(cells_along(s->h.L[a], s->cell_min, sc));
         if (std::find(seen.begin(), seen.end(), grid) != seen.end()) continue;
         seen.push_back(grid);
         for (auto* s : live(g)) RET(regrid(s, sc));
@@ -1268,7 +1352,7 @@ int gbmd_destroy(gbmd_system* s) {
     Group* g = s->own;
     destroy_graphs(g);
     cudaFree(g->d_desc); cudaFree(g->d_tp); cudaFree(g->d_tf); cudaFree(g->d_tc); cudaFree(g->d_te); cudaFree(g->d_nhpart);
-    cudaFree(g->d_ts); cudaFree(g->d_tb); cudaFree(g->d_tbk); cudaFree(g->d_partials);
+    cudaFree(g->d_ts); cudaFree(g->d_tb); cudaFree(g->d_tbk); cudaFree(g->d_tt); cudaFree(g->d_partials);
     cudaFree(g->d_ctl);
     delete g;
   }
@@ -1421,6 +1505,7 @@ int gbmd_get_info(gbmd_system* s, gbmd_info* out) {
   out->force_path = s->h.staged ? 1 : 0;
   out->max_window = f.max_window;
   out->cell_scale = s->cell_scale;
+  out->nlist = s->h.tree ? GBMD_NLIST_TREE : GBMD_NLIST_CELL;
   return GBMD_OK;
 }
 
@@ -1642,7 +1727,7 @@ int gbmd_batch_destroy(gbmd_batch* bh) {
   }
   destroy_graphs(b);
   cudaFree(b->d_desc); cudaFree(b->d_tp); cudaFree(b->d_tf); cudaFree(b->d_tc); cudaFree(b->d_te); cudaFree(b->d_nhpart);
-  cudaFree(b->d_ts); cudaFree(b->d_tb); cudaFree(b->d_tbk); cudaFree(b->d_partials);
+  cudaFree(b->d_ts); cudaFree(b->d_tb); cudaFree(b->d_tbk); cudaFree(b->d_tt); cudaFree(b->d_partials);
   cudaFree(b->d_ctl);
   delete b;
   return GBMD_OK;

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/gbmd.h"
+#include "tree_core.cuh"
 
 namespace gbmd {
 
@@ -33,7 +34,8 @@ constexpr int MAXT = GBMD_MAX_TYPES;
 constexpr int MAXT2 = MAXT * MAXT;
 
 // error codes stored in Flags::error (positive on the device)
-enum DevError : int { DEV_OK = 0, DEV_OVERFLOW = 1, DEV_NONFINITE = 2, DEV_BADTYPE = 3, DEV_WINDOW = 4 };
+enum DevError : int { DEV_OK = 0, DEV_OVERFLOW = 1, DEV_NONFINITE = 2, DEV_BADTYPE = 3, DEV_WINDOW = 4,
+                      DEV_TREE = 5 /* a tree traversal ran past its node bound */ };
 
 // staged force tiles: aligned 2x2x2 blocks of cells; their 4x4x4-cell window is
 // staged in shared memory (at most window_cap particles)
@@ -110,6 +112,18 @@ struct SysDev {
   float rbuff_half2;       // (r_buff / 2)^2, slightly reduced (conservative)
   int nc[3];               // cells per axis
   int ncells;
+  // sort bins of the cell list: ncells, or ntypes * ncells (type-major: bin =
+  // type * ncells + cell rank) for the tree neighbour list
+  int nbins;
+  // tree neighbour list (k_tree.cu; tree_core.cuh): after each sort, type t's
+  // particles are members[tree_first[t] .. + tree_n[t]); its tree has tree_P[t]
+  // leaves (global leaf numbers tree_leaf0[t] ..) and boxes
+  // tree_box[tree_node0[t] + 1 .. + 2 tree_P[t] - 1]
+  int tree;
+  int tree_first[MAXT], tree_n[MAXT], tree_P[MAXT], tree_leaf0[MAXT], tree_node0[MAXT];
+  int tree_leaves_total;
+  TreeBox* tree_box;
+  unsigned* tree_arrive;   // per node: children arrived during the build (reset to 0)
   int n, ntypes, cap, precision;
   int nl_stride;           // particles per slot group of the list (N rounded up to 32)
   // staged force path (mixed precision, >= 4 cells per axis): the list holds 16-bit

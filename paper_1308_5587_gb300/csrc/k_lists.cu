@@ -18,6 +18,7 @@
 //     (and rounding) as the brute-force reference definition, and appended after
 //     the other hits of their chunk of 32 candidates.
 #include "launch.cuh"
+#include "nlist_core.cuh"
 
 namespace gbmd {
 
@@ -30,16 +31,9 @@ static void put(KernelCall& k, const T& v) {
   ++k.nargs;
 }
 
-__device__ __forceinline__ bool rebuilding(const SysDev& s) {
-  return ((const volatile Flags*)s.flags)->do_rebuild != 0;
-}
 __device__ __forceinline__ bool sorting(const SysDev& s) {
   const FlagWords w = load_flag_words(s.flags);
   return w.do_rebuild != 0 && w.do_sort != 0;
-}
-__device__ __forceinline__ void count(const SysDev& s, const Tile& t, GroupCtl* ctl) {
-  if (threadIdx.x == 0 && t.first == 0) atomicAdd(&s.flags->launches, 1ull);
-  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
 }
 
 // ---- binning + histogram ----
@@ -54,12 +48,13 @@ __global__ void __launch_bounds__(TILE_P) k_bin(const SysDev* __restrict__ sysv,
   const int cx = cell_of_fixed(q.x, s.nc[0]);
   const int cy = cell_of_fixed(q.y, s.nc[1]);
   const int cz = cell_of_fixed(q.z, s.nc[2]);
-  const int r = s.lin2rank[(cz * s.nc[1] + cy) * s.nc[0] + cx];
+  // the tree list sorts type-major (each type's particles contiguous, in cell order)
+  const int r = s.lin2rank[(cz * s.nc[1] + cy) * s.nc[0] + cx] + (s.tree ? q.w * s.ncells : 0);
   s.key[i] = r;
   atomicAdd(&s.cell_cnt[r], 1);
 }
 
-// ---- exclusive scan of the cell counts (one block per system) ----
+// ---- exclusive scan of the bin counts (one block per system) ----
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SysDev* __restrict__ sysv,
                                                        const Tile* __restrict__ tiles,
                                                        GroupCtl* ctl) {
@@ -76,7 +71,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SysDev* __restrict_
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nc = s.ncells;
+  const int nc = s.nbins;
   for (int base = 0; base < nc; base += SCAN_THREADS) {
     const int c = base + threadIdx.x;
     const int v = c < nc ? s.cell_cnt[c] : 0;
@@ -260,23 +255,6 @@ __global__ void __launch_bounds__(256) k_blocks(const SysDev* __restrict__ sysv,
   }
 }
 
-// ---- FP64 decision for a candidate in the band: the reference definition ----
-__device__ __noinline__ bool exact_within(const SysDev& s, int i, int j, double rl2) {
-  const int n = s.n;
-  double d[3];
-  for (int a = 0; a < 3; ++a) {
-    const double sc = s.L[a] * (1.0 / 4294967296.0);
-    const double xi = __dmul_rn(s.x[a * n + i], sc);
-    const double xj = __dmul_rn(s.x[a * n + j], sc);
-    double dd = __dsub_rn(xi, xj);
-    dd = __dsub_rn(dd, __dmul_rn(s.L[a], rint(__ddiv_rn(dd, s.L[a]))));
-    d[a] = dd;
-  }
-  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])),
-                              __dmul_rn(d[2], d[2]));
-  return r2 < rl2;
-}
-
 // ---- neighbour list: one warp per cell ----
 // Lanes are the cell's particles (up to 32 at a time).  The candidates -- the
 // members of the stencil cells in (dz, dy, dx) cell order and index order within
@@ -289,7 +267,6 @@ __device__ __noinline__ bool exact_within(const SysDev& s, int i, int j, double 
 // hits to its row, so each row holds its neighbours in (stencil cell, index)
 // order.  Candidates within a relative band of 1e-5 of r_list^2 are decided in
 // FP64 as the definition does (the FP32 error is below 2e-6 relative).
-constexpr float NL_BAND = 1e-5f;
 constexpr int NL_TYPE_SHIFT = 30;
 
 // fixed-point coordinate of the centre of cell c of nc along an axis
@@ -312,7 +289,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   const SysDev& s = sysv[t.sys];
   count(s, t, ctl);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (!rebuilding(s) || w >= t.count) return;
+  if (!rebuilding(s) || s.tree || w >= t.count) return;
   const int nt = s.ntypes;
   // r_list^2 (1 -+ band) per type pair (FP32)
   __shared__ float thr_lo[CELLS_PER_TILE][MAXT2], thr_hi[CELLS_PER_TILE][MAXT2];

@@ -26,7 +26,8 @@ inline void args_of(const KernelCall& k, void** a) {
   for (int i = 0; i < k.nargs; ++i) a[i] = const_cast<unsigned char*>(k.store[i]);
 }
 
-// cell list + sort + neighbour list (each a no-op for systems not rebuilding)
+// cell list + sort + neighbour list (each a no-op for systems not rebuilding); the
+// sort bins are cells, or (type, cell) pairs for systems on the tree list
 KernelCall bin_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
 KernelCall scan_call(const SysDev* d, const Tile* tiles_s, int nsys, GroupCtl* ctl);
 KernelCall scatter_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
@@ -37,6 +38,11 @@ KernelCall copyback_call(const SysDev* d, const Tile* tiles_p, int ntiles, Group
 KernelCall blocks_call(const SysDev* d, const Tile* tiles_b, int ntiles, GroupCtl* ctl);
 KernelCall nlist_call(const SysDev* d, const Tile* tiles_c, int ntiles, GroupCtl* ctl, bool rel,
                       bool multi, bool staged);
+// tree neighbour list (k_tree.cu): the boxes of every type's tree (one thread per
+// leaf; tiles over the system's leaves), then the list (one thread per particle in
+// cell order; tiles over particles)
+KernelCall tree_build_call(const SysDev* d, const Tile* tiles_l, int ntiles, GroupCtl* ctl);
+KernelCall tree_nlist_call(const SysDev* d, const Tile* tiles_p, int ntiles, GroupCtl* ctl);
 // pair force kernels.  MODE_FORCE: forces at the current positions (readouts);
 // MODE_EV: also energy / virial / v.v partial sums (+ per-particle arrays when the
 // descriptor has them); MODE_STEP: the step kernel -- forces, the velocity Verlet

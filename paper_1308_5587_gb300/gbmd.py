@@ -43,7 +43,7 @@ class gbmd_desc(C.Structure):
                 ("stream", C.c_void_p), ("device", C.c_int32), ("force_path", C.c_int32),
                 ("integrator", C.c_int32), ("kT", C.c_double), ("tau", C.c_double),
                 ("potential", C.c_int32), ("mie_n", C.c_void_p), ("mie_m", C.c_void_p),
-                ("kappa", C.c_void_p)]
+                ("kappa", C.c_void_p), ("nlist", C.c_int32)]
 
 
 GBMD_PATH_GLOBAL, GBMD_PATH_STAGED = 0, 1
@@ -53,6 +53,8 @@ INTEGRATORS = {"nve": GBMD_NVE, "nvt": GBMD_NVT}
 GBMD_POT_LJ, GBMD_POT_MIE, GBMD_POT_WCA, GBMD_POT_YUKAWA, GBMD_POT_GAUSS = range(5)
 POTENTIALS = {"lj": GBMD_POT_LJ, "mie": GBMD_POT_MIE, "wca": GBMD_POT_WCA,
               "yukawa": GBMD_POT_YUKAWA, "gauss": GBMD_POT_GAUSS}
+GBMD_NLIST_CELL, GBMD_NLIST_TREE = 0, 1
+NLISTS = {"cell": GBMD_NLIST_CELL, "tree": GBMD_NLIST_TREE}
 
 
 class gbmd_thermo(C.Structure):
@@ -75,7 +77,7 @@ class gbmd_info(C.Structure):
                 ("step", C.c_int64), ("n_rebuilds", C.c_int64), ("n_sorts", C.c_int64),
                 ("kernel_launches", C.c_int64), ("neighbors_total", C.c_int64),
                 ("footprint_bytes", C.c_int64), ("force_path", C.c_int32),
-                ("max_window", C.c_int32), ("cell_scale", C.c_double)]
+                ("max_window", C.c_int32), ("cell_scale", C.c_double), ("nlist", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -165,7 +167,7 @@ def _stream_handle(stream):
 def make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass, precision,
               sort_period=0, nlist_capacity=0, threads_per_particle=0, stream=None,
               image=None, device=False, cuda_device=-1, force_path="global", integrator="nve",
-              kT=0.0, tau=0.0, potential="lj", mie_n=None, mie_m=None, kappa=None):
+              kT=0.0, tau=0.0, potential="lj", mie_n=None, mie_m=None, kappa=None, nlist="cell"):
     """Build a gbmd_desc; returns (desc, keepalive) -- keep the second alive.  Pair
     tables are ntypes x ntypes arrays or scalars; a table the potential does not read
     may be None (sigma for Yukawa, rcut for WCA, mie_n / mie_m / kappa elsewhere)."""
@@ -210,6 +212,7 @@ def make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass, preci
     d.tau = float(tau)
     d.potential = POTENTIALS.get(potential, potential) if isinstance(potential, str) else int(potential)
     d.mie_n, d.mie_m, d.kappa = _ptr(mie_n), _ptr(mie_m), _ptr(kappa)
+    d.nlist = NLISTS.get(nlist, nlist) if isinstance(nlist, str) else int(nlist)
     return d, keep
 
 
@@ -390,12 +393,12 @@ class System:
                  dt=0.005, mass=1.0, precision="mixed", sort_period=0, nlist_capacity=0,
                  threads_per_particle=0, stream=None, image=None, device=False, n=None,
                  cuda_device=-1, force_path="global", integrator="nve", kT=0.0, tau=0.0,
-                 potential="lj", mie_n=None, mie_m=None, kappa=None):
+                 potential="lj", mie_n=None, mie_m=None, kappa=None, nlist="cell"):
         n = int(n if n is not None else np.asarray(pos).reshape(-1, 3).shape[0])
         desc, keep = make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass,
                                precision, sort_period, nlist_capacity, threads_per_particle,
                                stream, image, device, cuda_device, force_path, integrator, kT, tau,
-                               potential, mie_n, mie_m, kappa)
+                               potential, mie_n, mie_m, kappa, nlist)
         self.n = n
         self.box = np.broadcast_to(np.asarray(box, np.float64), (3,)).copy()
         self.precision = precision

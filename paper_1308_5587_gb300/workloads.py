@@ -195,6 +195,61 @@ def potential_64k(kind: str, seed: int = BASE_SEED) -> Workload:
     return w
 
 
+def colloid_mixture(n_small: int, ratio: float = 5.0, phi_small: float = 0.2,
+                    phi_large: float = 0.2, T: float = 1.0, seed: int = BASE_SEED,
+                    r_buff: float = 0.4, dt: float = 0.002) -> Workload:
+    """Size-disperse binary WCA mixture (the case the tree list is for, Section 5):
+    small particles of diameter 1 (type 0) and large ones of diameter `ratio`
+    (type 1) at volume fractions phi_small and phi_large; sigma_ij = (d_i + d_j)/2,
+    eps = 1, r_cut,ij = 2^(1/6) sigma_ij, mass 1.
+
+    Large particles sit on a simple cubic lattice (a seeded subset of its sites,
+    jitter 0.05); small ones on a seeded subset of the FCC sites of spacing set by
+    the small density that keep a distance >= 0.55 (1 + ratio) from every large one
+    (jitter 0.05)."""
+    rp, rv, rs = _streams(seed, 3)
+    vs, vl = math.pi / 6.0, math.pi / 6.0 * ratio ** 3
+    n_large = max(1, int(round(n_small * (phi_large / vl) / (phi_small / vs))))
+    vol = n_small * vs / phi_small
+    L = vol ** (1.0 / 3.0)
+    box = np.full(3, L)
+    m = int(math.ceil(n_large ** (1.0 / 3.0) - 1e-9))
+    g = np.arange(m)
+    big = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) * (L / m)
+    big = big[np.sort(rs.choice(big.shape[0], n_large, replace=False))] - 0.5 * L
+    big += rs.uniform(-0.05, 0.05, big.shape)
+    # small-particle sites: every FCC site of m^3 cells (at least twice as many sites as
+    # small particles), minus the excluded shells
+    m = int(math.ceil((2.0 * n_small / 4.0) ** (1.0 / 3.0) - 1e-9))
+    a = L / m
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    g = np.arange(m)
+    cells = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    sites = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3) * a - 0.5 * L + 0.25 * a
+    from scipy.spatial import cKDTree   # periodic search of the excluded sites
+    tree = cKDTree(np.mod(sites + 0.5 * L, L), boxsize=L)
+    drop = tree.query_ball_point(np.mod(big + 0.5 * L, L), 0.55 * (1.0 + ratio))
+    keep = np.ones(sites.shape[0], bool)
+    for d in drop:
+        keep[d] = False
+    sites = sites[keep]
+    if sites.shape[0] < n_small:
+        raise ValueError("colloid_mixture: too few free sites for the small particles")
+    small = sites[np.sort(rp.choice(sites.shape[0], n_small, replace=False))]
+    small += rp.uniform(-0.05, 0.05, small.shape)
+    pos = np.concatenate([small, big])
+    pos -= L * np.floor((pos + 0.5 * L) / L)
+    n = pos.shape[0]
+    types = np.concatenate([np.zeros(n_small, np.int32), np.ones(n_large, np.int32)])
+    vel = maxwell_boltzmann(n, T, 1.0, rv)
+    d = np.array([1.0, ratio])
+    sig = 0.5 * (d[:, None] + d[None, :])
+    pairs = PairTable(np.ones((2, 2)), sig, 2.0 ** (1.0 / 6.0) * sig, "wca")
+    return Workload(pos, vel, types, box, pairs, r_buff, dt, 1.0, seed,
+                    {"ratio": ratio, "phi_small": phi_small, "phi_large": phi_large, "T": T,
+                     "n_large": n_large})
+
+
 def replica_params(count: int = 256, seed: int = BASE_SEED, n_lo: int = 500, n_hi: int = 20000):
     """(N_k, rho_k, T_k, seed_k) for the batched-ensemble shape."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -85,6 +85,8 @@ def _desc(lib, **over):
     (dict(potential="lj", rcut=None), "BAD_ARG"),
     (dict(potential="mie", mie_n=12.0, mie_m=6.0, eps=-1.0), "BAD_ARG"),
     (dict(potential="wca", rcut=None, box=3.0), "BOX_TOO_SMALL"),     # 2 (2^(1/6) + 0.4) > 3
+    (dict(nlist=2), "BAD_ARG"),
+    (dict(nlist="tree", types=np.array([0, 1, 0, 0], np.int32)), "BAD_ARG"),
 ])
 def test_create_rejects_bad_arguments_on_the_host(lib, bad, status):
     d, keep = _desc(lib, **bad)
@@ -120,3 +122,12 @@ def test_footprint_follows_the_potential_cut(lib):
     f_lj, f_wca = lib.gbmd_footprint_bytes(lj), lib.gbmd_footprint_bytes(wca)
     assert 0 < f_wca < f_lj
     assert lib.gbmd_footprint_bytes(yuk) == f_lj   # same r_cut, same layout
+
+
+def test_footprint_of_the_tree_list(lib):
+    """The tree list's cells only order the particles (finer grid, type-major bins)
+    and it holds its boxes: about 36 bytes per particle more than the cell list."""
+    cell, k1 = _desc(lib, n=8000, box=24.0)
+    tree, k2 = _desc(lib, n=8000, box=24.0, nlist="tree")
+    fc, ft = lib.gbmd_footprint_bytes(cell), lib.gbmd_footprint_bytes(tree)
+    assert 8000 * 30 < ft - fc < 8000 * 60
