@@ -50,6 +50,25 @@ def check_neighbors(s, w):
     return len(ref)
 
 
+def check_verlet(s, w):
+    """Between builds: the list was built at earlier positions, and no particle has
+    moved r_buff/2 since, so it holds every pair now within r_cut and none now
+    beyond r_list + r_buff."""
+    pos = s.state()[0]
+    counts, idx = s.neighbors(cap=int(s.info()["nlist_capacity"]) + 8)
+    rc = oracle.cutoffs(w.pairs.as_dict())
+    pairs, r = oracle.neighbors(pos, w.box, w.types, rc)
+    inner = r < rc[w.types[pairs[:, 0]], w.types[pairs[:, 1]]] - 1e-9
+    must = {(int(a), int(b)) for a, b in pairs[inner]}
+    pairs, r = oracle.neighbors(pos, w.box, w.types, rc + 2 * w.r_buff + 1e-9)
+    may = {(int(a), int(b)) for a, b in pairs}
+    mine = set()
+    for i in range(w.n):
+        mine.update((min(i, int(j)), max(i, int(j))) for j in idx[i, :counts[i]])
+    assert must <= mine, len(must - mine)
+    assert mine <= may
+
+
 def check_forces(s, w, prec):
     pos = s.state()[0]
     F = s.forces()
@@ -79,10 +98,13 @@ def test_tree_neighbor_sets_and_forces(case, prec):
     assert s.info()["force_path"] == 0
     check_neighbors(s, w)
     check_forces(s, w, prec)
-    s.step(150)   # rebuilds (and a re-sort) at the GPU's own positions
+    s.step(150)   # rebuilds at the GPU's own positions (no re-sort: cell order changes)
     assert s.info()["n_rebuilds"] >= 1
-    check_neighbors(s, w)
+    check_verlet(s, w)
     check_forces(s, w, prec)
+    pos, vel, img, step = s.state()   # a rebuild at these positions, then the exact set
+    s.set_state(pos, vel, img, step)
+    check_neighbors(s, w)
     s.close()
 
 
@@ -181,5 +203,6 @@ def test_tree_with_nvt():
     s.step(200)
     th = s.thermo()
     assert th["step"] == 200 and np.isfinite(th["h_ext"])
-    check_neighbors(s, w)
+    check_verlet(s, w)
+    check_forces(s, w, "mixed")
     s.close()
