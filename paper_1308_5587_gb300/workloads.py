@@ -218,9 +218,11 @@ def colloid_mixture(n_small: int, ratio: float = 5.0, phi_small: float = 0.2,
     big = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) * (L / m)
     big = big[np.sort(rs.choice(big.shape[0], n_large, replace=False))] - 0.5 * L
     big += rs.uniform(-0.05, 0.05, big.shape)
-    # small-particle sites: every FCC site of m^3 cells (at least twice as many sites as
-    # small particles), minus the excluded shells
-    m = int(math.ceil((2.0 * n_small / 4.0) ** (1.0 / 3.0) - 1e-9))
+    # small-particle sites: every FCC site of m^3 cells (1.1 times as many sites as
+    # small particles outside the excluded shells), minus those shells
+    rmin = 0.55 * (1.0 + ratio)
+    excl = min(0.9, n_large * 4.0 / 3.0 * math.pi * rmin ** 3 / vol)
+    m = int(math.ceil((1.1 * n_small / (1.0 - excl) / 4.0) ** (1.0 / 3.0) - 1e-9))
     a = L / m
     basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
     g = np.arange(m)
@@ -228,7 +230,7 @@ def colloid_mixture(n_small: int, ratio: float = 5.0, phi_small: float = 0.2,
     sites = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3) * a - 0.5 * L + 0.25 * a
     from scipy.spatial import cKDTree   # periodic search of the excluded sites
     tree = cKDTree(np.mod(sites + 0.5 * L, L), boxsize=L)
-    drop = tree.query_ball_point(np.mod(big + 0.5 * L, L), 0.55 * (1.0 + ratio))
+    drop = tree.query_ball_point(np.mod(big + 0.5 * L, L), rmin)
     keep = np.ones(sites.shape[0], bool)
     for d in drop:
         keep[d] = False

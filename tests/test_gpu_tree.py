@@ -85,7 +85,7 @@ WORKLOADS = {
     "ka1200": lambda: wl.lj_fluid(1200, 1.2, 1.0, seed=92, binary=True, r_buff=0.3),
     "lj256_small_box": lambda: wl.lj_fluid(256, 0.9, 1.2, seed=93),
     "colloid_1to5": lambda: wl.colloid_mixture(3000, ratio=5.0, seed=94),
-    "colloid_1to3": lambda: wl.colloid_mixture(4000, ratio=3.0, phi_small=0.3, seed=95),
+    "colloid_1to3": lambda: wl.colloid_mixture(4000, ratio=3.0, seed=95),
 }
 
 
