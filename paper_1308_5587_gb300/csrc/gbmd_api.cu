@@ -682,9 +682,9 @@ Geometry geometry(const gbmd_desc* d, const int64_t* type_counts = nullptr) {
   }
   const double vol = d->box[0] * d->box[1] * d->box[2];
   g.rl_max = rmax + d->r_buff;
-  // the tree list's cells only order the particles: as fine as the smallest r_list,
-  // but not much finer than two particles per cell
-  g.cell_min = tree ? std::max(rmin + d->r_buff, std::cbrt(2.0 * vol / (double)d->n)) : g.rl_max;
+  // the tree list's cells only order the particles (by Morton code inside a cell):
+  // about 32 particles per cell, and no finer than the smallest r_list
+  g.cell_min = tree ? std::max(rmin + d->r_buff, std::cbrt(32.0 * vol / (double)d->n)) : g.rl_max;
   g.ncells = 1;
   for (int a = 0; a < 3; ++a) {
     g.nc[a] = cells_along(d->box[a], g.cell_min, 1.0);
@@ -732,8 +732,8 @@ size_t footprint_of(const gbmd_desc* d, const Geometry& g) {
   b += n * (d->precision == GBMD_FP64 ? 32 : 16);   // force
   b += n * 4 + round_up(n, 32) * 4 * (size_t)g.cap;  // nn, nl (ELL4)
   b += n * 4 * 4 + (size_t)(g.nbins + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;   // cells
-  if (d->nlist == GBMD_NLIST_TREE)   // tree boxes and arrival counters (<= n + 4 ntypes nodes)
-    b += (n + 4 * (size_t)d->ntypes) * (sizeof(TreeBox) + 4);
+  if (d->nlist == GBMD_NLIST_TREE)   // tree boxes and arrival counters (<= n + 4 ntypes
+    b += (n + 4 * (size_t)d->ntypes) * (sizeof(TreeBox) + 4) + n * 4;   // nodes), fine keys
   b += (size_t)((g.nc[0] + 1) / 2) * ((g.nc[1] + 1) / 2) * ((g.nc[2] + 1) / 2) *
        (WIN_CELLS * 8 + 16);                                                      // staged blocks
   b += n * (8 * 3 * 2 + 4 * 3 + 4 * 2 + 16);         // re-sort scratch
@@ -935,6 +935,7 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   if (tree) {
     A((void**)&h.tree_box, (size_t)nodes * sizeof(TreeBox));
     A((void**)&h.tree_arrive, (size_t)nodes * 4);
+    A((void**)&h.fkey, N * 4);
   }
   A((void**)&s->d_flags, sizeof(Flags));
   A((void**)&s->d_pos, N * 24); A((void**)&s->d_vel, N * 24); A((void**)&s->d_frc, N * 24);

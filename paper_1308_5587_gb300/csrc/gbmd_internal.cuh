@@ -124,6 +124,7 @@ struct SysDev {
   int tree_leaves_total;
   TreeBox* tree_box;
   unsigned* tree_arrive;   // per node: children arrived during the build (reset to 0)
+  unsigned* fkey;          // [N] the particle's fine Morton code at the last build
   int n, ntypes, cap, precision;
   int nl_stride;           // particles per slot group of the list (N rounded up to 32)
   // staged force path (mixed precision, >= 4 cells per axis): the list holds 16-bit

@@ -36,6 +36,21 @@ __device__ __forceinline__ bool sorting(const SysDev& s) {
   return w.do_rebuild != 0 && w.do_sort != 0;
 }
 
+// Morton code of the top 10 bits of each fixed-point coordinate (on [0, 2^32))
+__device__ __forceinline__ unsigned spread10(unsigned v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__device__ __forceinline__ unsigned fine_morton(const int4& q) {
+  return spread10(((unsigned)q.x ^ 0x80000000u) >> 22) |
+         (spread10(((unsigned)q.y ^ 0x80000000u) >> 22) << 1) |
+         (spread10(((unsigned)q.z ^ 0x80000000u) >> 22) << 2);
+}
+
 // ---- binning + histogram ----
 __global__ void __launch_bounds__(TILE_P) k_bin(const SysDev* __restrict__ sysv,
                                                 const Tile* __restrict__ tiles, GroupCtl* ctl) {
@@ -49,8 +64,10 @@ __global__ void __launch_bounds__(TILE_P) k_bin(const SysDev* __restrict__ sysv,
   const int cy = cell_of_fixed(q.y, s.nc[1]);
   const int cz = cell_of_fixed(q.z, s.nc[2]);
   // the tree list sorts type-major (each type's particles contiguous, in cell order)
+  // and, inside a bin, by the particle's own Morton code (the leaves' order)
   const int r = s.lin2rank[(cz * s.nc[1] + cy) * s.nc[0] + cx] + (s.tree ? q.w * s.ncells : 0);
   s.key[i] = r;
+  if (s.tree) s.fkey[i] = fine_morton(q);
   atomicAdd(&s.cell_cnt[r], 1);
 }
 
@@ -117,7 +134,9 @@ __global__ void __launch_bounds__(TILE_P) k_scatter(const SysDev* __restrict__ s
   s.members_tmp[p] = i;
 }
 
-// ---- sort each cell's members by index (warp per cell) -> stable order ----
+// ---- sort each bin's members (warp per bin) -> a deterministic order ----
+// By particle index (the stable order); on the tree list by (fine Morton code,
+// index), so that consecutive members of a bin are spatial neighbours.
 __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* __restrict__ sysv,
                                                                   const Tile* __restrict__ tiles,
                                                                   GroupCtl* ctl) {
@@ -128,10 +147,16 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* 
   if (!rebuilding(s) || w >= t.count) return;
   const int r = t.first + w;
   const int b = s.cell_start[r], e = s.cell_start[r + 1], n = e - b;
+  const bool fine = s.tree != 0;
+  // the sort key of member m: (fine code, index) or the index alone
+  auto key = [&](int v) -> unsigned long long {
+    return ((unsigned long long)(fine ? s.fkey[v] : 0u) << 32) | (unsigned)v;
+  };
   if (n <= 32) {
     const int v = lane < n ? s.members_tmp[b + lane] : 0x7fffffff;
+    const unsigned long long kv = lane < n ? key(v) : ~0ull;
     int rk = 0;
-    for (int k = 0; k < 32; ++k) rk += __shfl_sync(0xffffffffu, v, k) < v;
+    for (int k = 0; k < 32; ++k) rk += __shfl_sync(0xffffffffu, kv, k) < kv;
     if (lane < n) {
       s.members[b + rk] = v;
       s.rmember[v] = b + rk;
@@ -139,8 +164,9 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* 
   } else {
     for (int m = lane; m < n; m += 32) {
       const int v = s.members_tmp[b + m];
+      const unsigned long long kv = key(v);
       int rk = 0;
-      for (int k = 0; k < n; ++k) rk += s.members_tmp[b + k] < v;
+      for (int k = 0; k < n; ++k) rk += key(s.members_tmp[b + k]) < kv;
       s.members[b + rk] = v;
       s.rmember[v] = b + rk;
     }

@@ -1,8 +1,9 @@
 // k_tree.cu -- the tree neighbour list (Section 5: nlist.tree, a bounding volume
 // hierarchy per particle type, for size-disperse systems).
 //
-// After the cell sort (k_bin .. k_cellsort, type-major bins), type t's particles
-// are members[tree_first[t] .. + tree_n[t]) in Morton cell order.  Its tree is the
+// After the cell sort (k_bin .. k_cellsort, type-major bins, Morton order of the
+// particles inside a bin), type t's particles are members[tree_first[t] ..
+// + tree_n[t]) in Morton order of cells, then of particles.  Its tree is the
 // implicit complete binary tree of tree_core.cuh over them, TREE_LEAF particles per
 // leaf.  Two kernels, both no-ops for systems not rebuilding or on the cell list:
 //   k_tree_build  one thread per leaf: the leaf's box, then up the tree: the second

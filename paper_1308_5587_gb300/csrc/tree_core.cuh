@@ -7,8 +7,9 @@
 // bounding volume hierarchy (nlist.tree), one tree per particle type, each particle
 // querying every type's tree with its own search radius.  Here the tree of a type is
 // an implicit complete binary tree (heap numbering: root 1, children 2k and 2k + 1)
-// over that type's particles in the order of the cell sort (Morton order of cells),
-// TREE_LEAF particles per leaf; P leaves (P a power of two, the last ones empty).
+// over that type's particles in the order of the cell sort (Morton order of the cells,
+// then of the particles inside a cell), TREE_LEAF particles per leaf; P leaves (P a
+// power of two, the last ones empty).
 // A node holds the axis-aligned box of its particles in 32-bit fixed point
 // (u = q + 2^31 mod 2^32, i.e. the box [-L/2, L/2) mapped onto [0, 2^32)); an
 // empty node has lo > hi on x.
@@ -23,7 +24,10 @@
 
 namespace gbmd {
 
-constexpr int TREE_LEAF = 4;   // particles per leaf
+#ifndef GBMD_TREE_LEAF
+#define GBMD_TREE_LEAF 4
+#endif
+constexpr int TREE_LEAF = GBMD_TREE_LEAF;   // particles per leaf
 
 // node box: lo in (x, y, z), hi in (x2, y2, z2); 32 bytes, two 16-byte loads
 struct alignas(16) TreeBox {
