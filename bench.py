@@ -155,13 +155,14 @@ def make_workload(name: str, rank: int):
     if name == "plain4k":
         return wl.plain_fp64_4k(seed), "fp64", 0, \
             "lj_fluid N=4000 rho=0.84 T=1.2 rc=2.5 shifted rbuff=0.4 dt=0.005 fp64"
-    if name in ("colloid250k", "colloid250k_cell"):   # size-disperse: the tree list's case
-        w = wl.colloid_mixture(250000, ratio=5.0, seed=seed)
+    if name in COLLOID_WORKLOADS:   # size-disperse: the tree list's case
+        ratio = 10.0 if "_r10" in name else 5.0
+        w = wl.colloid_mixture(250000, ratio=ratio, seed=seed)
         nl = "cell" if name.endswith("_cell") else "tree"
         w.meta["nlist"] = nl
         return w, "mixed", 100, \
-            (f"wca_colloid_mixture N={w.n} (250000 d=1 + {w.meta['n_large']} d=5) phi=0.2+0.2 "
-             f"T=1.0 rc=2^(1/6)sigma_ij rbuff=0.4 dt=0.002 nlist={nl}")
+            (f"wca_colloid_mixture N={w.n} (250000 d=1 + {w.meta['n_large']} d={ratio:g}) "
+             f"phi=0.2+0.2 T=1.0 rc=2^(1/6)sigma_ij rbuff=0.4 dt=0.002 nlist={nl}")
     if name in POTENTIAL_WORKLOADS:   # the other pair potentials on the LJ 64k geometry
         w = wl.potential_64k(name[:-3], seed)
         return w, "mixed", 100, f"{name[:-3]}_fluid N=64000 rho=0.84 T=1.2 {w.meta['pair']} " \
@@ -174,6 +175,7 @@ def make_workload(name: str, rank: int):
 
 
 POTENTIAL_WORKLOADS = ("mie64k", "wca64k", "yukawa64k", "gauss64k")
+COLLOID_WORKLOADS = ("colloid250k", "colloid250k_cell", "colloid250k_r10", "colloid250k_r10_cell")
 
 
 def system_kw(w):
@@ -689,7 +691,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["gbmd", "reference"], default="gbmd")
     ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k", "paper64k", "paper64k_mixed",
-                                           *POTENTIAL_WORKLOADS, "colloid250k", "colloid250k_cell",
+                                           *POTENTIAL_WORKLOADS, *COLLOID_WORKLOADS,
                                            "batch", "serve"],
                     default="lj64k")
     ap.add_argument("--replicas", type=int, default=256, help="batch workload: replicas")

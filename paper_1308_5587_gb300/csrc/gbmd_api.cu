@@ -733,7 +733,7 @@ size_t footprint_of(const gbmd_desc* d, const Geometry& g) {
   b += n * 4 + round_up(n, 32) * 4 * (size_t)g.cap;  // nn, nl (ELL4)
   b += n * 4 * 4 + (size_t)(g.nbins + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;   // cells
   if (d->nlist == GBMD_NLIST_TREE)   // tree boxes and arrival counters (<= n + 4 ntypes
-    b += (n + 4 * (size_t)d->ntypes) * (sizeof(TreeBox) + 4) + n * 4;   // nodes), fine keys
+    b += (n + 4 * (size_t)d->ntypes) * (sizeof(TreeBox) + 4) + n * 20;  // nodes), keys, leaves
   b += (size_t)((g.nc[0] + 1) / 2) * ((g.nc[1] + 1) / 2) * ((g.nc[2] + 1) / 2) *
        (WIN_CELLS * 8 + 16);                                                      // staged blocks
   b += n * (8 * 3 * 2 + 4 * 3 + 4 * 2 + 16);         // re-sort scratch
@@ -879,6 +879,25 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
       nodes += 2 * h.tree_P[t];   // boxes 1 .. 2P - 1 (0 unused)
     }
     h.tree_leaves_total = leaves;
+    // query order: the types by decreasing expected work per particle
+    double work[GBMD_MAX_TYPES];
+    int ord[GBMD_MAX_TYPES];
+    for (int t = 0; t < nt; ++t) {
+      work[t] = 0;
+      for (int u = 0; u < nt; ++u) {
+        const double rl = cut_of(d, t * nt + u) + d->r_buff;
+        work[t] += (double)tcount[u] * rl * rl * rl;
+      }
+      ord[t] = t;
+    }
+    std::stable_sort(ord, ord + nt, [&](int a, int b) { return work[a] > work[b]; });
+    int qpos = 0;
+    for (int k = 0; k < nt; ++k) {
+      h.tree_qtype[k] = ord[k];
+      h.tree_qpos[k] = qpos;
+      qpos += (int)tcount[ord[k]];
+    }
+    h.tree_qpos[nt] = qpos;
   }
   h.nvt = d->integrator == GBMD_NVT;
   h.kT = d->kT;
@@ -936,6 +955,7 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
     A((void**)&h.tree_box, (size_t)nodes * sizeof(TreeBox));
     A((void**)&h.tree_arrive, (size_t)nodes * 4);
     A((void**)&h.fkey, N * 4);
+    A((void**)&h.tree_q, N * 16);
   }
   A((void**)&s->d_flags, sizeof(Flags));
   A((void**)&s->d_pos, N * 24); A((void**)&s->d_vel, N * 24); A((void**)&s->d_frc, N * 24);

@@ -125,6 +125,11 @@ struct SysDev {
   TreeBox* tree_box;
   unsigned* tree_arrive;   // per node: children arrived during the build (reset to 0)
   unsigned* fkey;          // [N] the particle's fine Morton code at the last build
+  int4* tree_q;            // [N] the leaves' particles in leaf order: (x, y, z, index)
+  // the list kernel visits the types in decreasing order of their expected query work
+  // (sum over t of n_t r_list(type, t)^3): launch positions tree_qpos[k] .. belong to
+  // type tree_qtype[k]
+  int tree_qpos[MAXT + 1], tree_qtype[MAXT];
   int n, ntypes, cap, precision;
   int nl_stride;           // particles per slot group of the list (N rounded up to 32)
   // staged force path (mixed precision, >= 4 cells per axis): the list holds 16-bit

@@ -6,14 +6,16 @@
 // + tree_n[t]) in Morton order of cells, then of particles.  Its tree is the
 // implicit complete binary tree of tree_core.cuh over them, TREE_LEAF particles per
 // leaf.  Two kernels, both no-ops for systems not rebuilding or on the cell list:
-//   k_tree_build  one thread per leaf: the leaf's box, then up the tree: the second
-//                 child to arrive at a node writes its box (an arrival counter per
-//                 node, which that child resets); no thread waits for another;
+//   k_tree_build  one thread per leaf: the leaf's box and a copy of its particles
+//                 (position, index) in leaf order, then up the tree: the second child
+//                 to arrive at a node writes its box (an arrival counter per node,
+//                 which that child resets); no thread waits for another;
 //   k_tree_nlist  one thread per particle, in cell order (neighbouring threads walk
-//                 similar paths): for every type t, the leaves of t's tree within
-//                 r_list(t_i, t) of the particle, then the same pair decision as the
-//                 cell list (nlist_core.cuh).  The row holds the neighbours in
-//                 (type, cell order) order.
+//                 similar paths), the types with the longest queries first (they
+//                 would otherwise finish last): for every type t, the leaves of t's
+//                 tree within r_list(t_i, t) of the particle, then the same pair
+//                 decision as the cell list (nlist_core.cuh).  The row holds the
+//                 neighbours in (type, cell order) order.
 // A traversal examines each node at most once, so 2 P nodes bound it; passing the
 // bound (which cannot happen) would stop it and set DEV_TREE.
 #include "launch.cuh"
@@ -63,8 +65,10 @@ __global__ void __launch_bounds__(TILE_P) k_tree_build(const SysDev* __restrict_
   for (int k = 0; k < TREE_LEAF; ++k) {
     const int m = b * TREE_LEAF + k;
     if (m < nty) {
-      const int4 q = qv[s.members[first + m]];
+      const int j = s.members[first + m];
+      const int4 q = qv[j];
       tree_box_add(box, tree_u(q.x), tree_u(q.y), tree_u(q.z));
+      s.tree_q[first + m] = make_int4(q.x, q.y, q.z, j);   // the leaf's own copy
     }
   }
   int node = P + b;
@@ -101,7 +105,12 @@ __global__ void __launch_bounds__(TILE_P) k_tree_nlist(const SysDev* __restrict_
   const bool valid = (int)threadIdx.x < t.count;
   unsigned long long nb = 0;
   if (valid) {
-    const int i = s.members[t.first + threadIdx.x];
+    // launch position -> member: the types in the order of tree_qtype
+    const int pos = t.first + threadIdx.x;
+    int k = 0;
+    while (k + 1 < nt && pos >= s.tree_qpos[k + 1]) ++k;
+    const int ty = s.tree_qtype[k];
+    const int i = s.members[s.tree_first[ty] + (pos - s.tree_qpos[k])];
     const int4* __restrict__ qv = q_at(s, step_of(s.flags));
     const int4 qi = qv[i];
     const uint32_t ux = tree_u(qi.x), uy = tree_u(qi.y), uz = tree_u(qi.z);
@@ -120,9 +129,9 @@ __global__ void __launch_bounds__(TILE_P) k_tree_nlist(const SysDev* __restrict_
             for (int k = 0; k < TREE_LEAF; ++k) {
               const int m = b * TREE_LEAF + k;
               if (m >= nty) break;
-              const int j = s.members[first + m];
+              const int4 qj = s.tree_q[first + m];
+              const int j = qj.w;
               if (j == i) continue;
-              const int4 qj = qv[j];
               const float dx = (float)min_image_fixed(qi.x, qj.x) * fs0;
               const float dy = (float)min_image_fixed(qi.y, qj.y) * fs1;
               const float dz = (float)min_image_fixed(qi.z, qj.z) * fs2;
