@@ -82,10 +82,16 @@ GBMD_HD float tree_gap2(const TreeBox& b, uint32_t ux, uint32_t uy, uint32_t uz,
   return gx * gx + gy * gy + gz * gz;
 }
 
-// the node after node k's subtree in depth-first order (left child first); 0 when
-// the traversal is over
+// the node after node k's subtree in depth-first order (left child first): up past
+// every right child (the trailing ones of k), then to the right sibling; 0 when the
+// traversal is over
 GBMD_HD int tree_next(int k) {
-  while (k & 1) k >>= 1;
+#if defined(__CUDA_ARCH__)
+  const int ones = __ffs(~k) - 1;
+#else
+  const int ones = __builtin_ctz(~(unsigned)k);
+#endif
+  k >>= ones;
   return k ? k + 1 : 0;
 }
 
