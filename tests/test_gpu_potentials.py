@@ -206,3 +206,44 @@ def test_batch_rejects_mixed_evaluators_and_staged_falls_back():
     assert s.info()["force_path"] == 1
     check(s, w, "mixed", "wca staged")
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("kind", ["mie", "yukawa", "gauss"])
+def test_potentials_on_the_tree_list(kind, prec):
+    """The evaluators and the tree neighbour list together: two types, then after
+    steps with rebuilds, against the oracle."""
+    w = fluid(kind, 3000, seed=66, binary=True, rho=1.0)
+    s = gbmd.System.from_workload(w, precision=prec, nlist="tree")
+    assert s.info()["nlist"] == gbmd.GBMD_NLIST_TREE
+    check(s, w, prec, f"{kind}/{prec}/tree")
+    s.step(120)
+    check(s, w, prec, f"{kind}/{prec}/tree after steps")
+    s.close()
+
+
+def test_mie_nvt_batch_members_match_alone():
+    ws = [fluid("mie", n, seed=75 + k) for k, n in enumerate((800, 1700))]
+    kw = dict(precision="mixed", integrator="nvt", kT=1.1, tau=0.7)
+    alone = []
+    for w in ws:
+        s = gbmd.System.from_workload(w, **kw)
+        s.set_tuning(2, 128)
+        s.step(50)
+        alone.append((s.state(), s.thermo()))
+        s.close()
+    b = gbmd.Batch("mixed")
+    b.set_tuning(2, 128)
+    ss = [gbmd.System.from_workload(w, **kw) for w in ws]
+    for s in ss:
+        b.add(s)
+    b.step(50)
+    b.sync()
+    for s, (st, th) in zip(ss, alone):
+        for x, y in zip(s.state()[:3], st[:3]):
+            assert np.array_equal(x, y)
+        t2 = s.thermo()
+        assert t2["xi"] == th["xi"] and t2["pe"] == th["pe"]
+    b.close()
+    for s in ss:
+        s.close()
