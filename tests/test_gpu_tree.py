@@ -206,3 +206,23 @@ def test_tree_with_nvt():
     check_verlet(s, w)
     check_forces(s, w, "mixed")
     s.close()
+
+
+def test_tree_autotune_and_cell_scale_keep_results():
+    """The autotuner's cell-width sweep regrids the tree list's sort cells (type-major
+    bins); the lists and forces stay those of the definition."""
+    w = WORKLOADS["colloid_1to3"]()
+    s = gbmd.System.from_workload(w, precision="mixed", nlist="tree")
+    s.step(20)
+    s.autotune(None)
+    info = s.info()
+    assert info["nlist"] == gbmd.GBMD_NLIST_TREE
+    assert info["cell_scale"] in (1.0, 1.1, 1.2, 1.35)
+    s.step(20)
+    check_verlet(s, w)
+    check_forces(s, w, "mixed")
+    s.set_cell_scale(1.35)
+    s.set_state(*s.state())   # a rebuild at the current positions, then the exact set
+    check_neighbors(s, w)
+    check_forces(s, w, "mixed")
+    s.close()
