@@ -365,8 +365,7 @@ def gpu_arm(args):
                                   stream=stream.cuda_stream, cuda_device=local,
                                   force_path=args.force_path, **system_kw(w))
     if args.autotune:
-        s.autotune(os.path.join(ROOT, "_work", "tune_cache.txt") if os.path.isdir(
-            os.path.join(ROOT, "_work")) else None)
+        s.autotune(args.tune_cache)
     clocks = ClockSampler(local)
     clocks.start()
     step_ms, _, launches = timed_steps(torch, s, args.steps, args.warmup, flush, stream, dist)
@@ -701,6 +700,8 @@ def main(argv=None):
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serve workload: HBM budget")
     ap.add_argument("--quantum", type=int, default=2000, help="serve workload: max steps per quantum")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--tune-cache", default=None,
+                    help="with --autotune: text file to read / append the tuning choices")
     ap.add_argument("--force-path", choices=["global", "staged"], default="global",
                     help="neighbour gather through L1/L2 by 32-bit index (default) or "
                          "from a shared-memory window by 16-bit index")
