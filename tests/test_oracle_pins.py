@@ -227,7 +227,7 @@ def test_free_flight_through_boundary(oracle):
     assert np.array_equal(out["vel"], vel)
 
 
-def _cluster():
+def _vv_cluster():
     pos = np.array([[0.0, 0.0, 0.0], [1.12, 0.05, 0.0], [0.5, 0.95, 0.1], [0.4, 0.4, 0.9]])
     vel = np.array([[0.3, -0.2, 0.1], [-0.1, 0.4, 0.0], [0.0, -0.3, 0.2], [-0.2, 0.1, -0.3]])
     return pos, vel, np.full(3, 40.0)
@@ -235,7 +235,7 @@ def _cluster():
 
 def test_verlet_matches_ode_solver_second_order(oracle):
     from scipy.integrate import solve_ivp
-    pos, vel, L = _cluster()
+    pos, vel, L = _vv_cluster()
     p = pair_params()
     T = 0.4
 
@@ -302,6 +302,44 @@ def test_ideal_gas_pressure(oracle):
     assert P == pytest.approx(len(pos) / 8000.0 * T, rel=1e-14)
 
 
+def test_virial_pressure_is_minus_volume_derivative_of_energy(oracle):
+    """At K = 0 the pressure is the configurational one, P = -dU/dV, with U(V) taken
+    under uniform scaling of the box and every position (V = lambda^3 V0): a
+    central difference in lambda fixes the sign, the 1/3 and the 1/V of the
+    virial term independently of how the oracle writes P."""
+    for seed in range(300, 400):
+        w = wl.lj_fluid(64, 0.6, 1.0, seed=seed, binary=True, jitter=0.2)
+        if _clear_of_cut(w.pos, w.box, w.types, w.pairs.rcut, 1e-4):
+            break
+    p = w.pairs.as_dict()
+    _, U, W, *_ = oracle.forces(w.pos, w.box, w.types, p)
+    h = 1e-7
+    up = oracle.forces(w.pos * (1 + h), w.box * (1 + h), w.types, p)[1]
+    dn = oracle.forces(w.pos * (1 - h), w.box * (1 - h), w.types, p)[1]
+    vol = float(np.prod(w.box))
+    dU_dV = (up - dn) / (2 * h) / (3 * vol)          # dV/dlambda = 3 V0 at lambda = 1
+    _, P = oracle.thermo(w.n, w.box, 0.0, W)
+    assert abs(W[0] + W[3] + W[5]) > 1.0              # a real virial, not the W = 0 case
+    assert P == pytest.approx(-dU_dV, rel=1e-6, abs=1e-9)
+
+
+def test_pair_pressure_closed_form(oracle):
+    """Two particles at r = sigma in an otherwise empty box: the pair virial is
+    r |F(r)| = 24 eps (Clausius), so at K = 0 P = 24 eps / (3 V) = 8 eps / V; adding
+    kinetic energy adds the ideal-gas part N T / V and nothing else."""
+    for eps in (1.0, 0.7):
+        pos, box = two_particles(1.0, axis=1, L=12.0)
+        _, _, W, _, _ = oracle.forces(pos, box, None, pair_params(eps=eps))
+        vol = 12.0 ** 3
+        T0, P0 = oracle.thermo(2, box, 0.0, W)
+        assert T0 == 0.0
+        assert P0 == pytest.approx(8.0 * eps / vol, rel=1e-12)
+        K = 1.7
+        T, P = oracle.thermo(2, box, K, W)
+        assert T == pytest.approx(2 * K / 3, rel=1e-14)        # 3N - 3 = 3 degrees of freedom
+        assert P == pytest.approx(P0 + 2 * T / vol, rel=1e-12)
+
+
 def test_oracle_thread_count_independent(oracle):
     w = wl.lj_fluid(400, 0.84, 1.2, seed=8)
     old = oracle.get_threads()
@@ -331,7 +369,7 @@ def test_nvt_weak_coupling_is_velocity_verlet(oracle):
     assert abs(a["xi"]) < 1e-20
 
 
-def _cluster():
+def _nvt_cluster():
     # four particles near the pair minimum, far from every cut-off and image
     pos = np.array([[0.0, 0.0, 0.0], [1.12, 0.0, 0.0], [0.56, 0.97, 0.0], [0.56, 0.32, 0.91]])
     vel = np.random.default_rng(8).normal(scale=0.3, size=(4, 3))
@@ -340,7 +378,7 @@ def _cluster():
 
 
 def test_nvt_extended_energy_is_conserved_at_second_order(oracle):
-    pos, vel, box = _cluster()
+    pos, vel, box = _nvt_cluster()
     p = pair_params()
     kT, tau, t_end = 0.5, 0.2, 0.4
     drift = []
