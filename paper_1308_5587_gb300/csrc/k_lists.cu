@@ -293,12 +293,42 @@ __global__ void __launch_bounds__(256) k_blocks(const SysDev* __restrict__ sysv,
 // hits to its row, so each row holds its neighbours in (stencil cell, index)
 // order.  Candidates within a relative band of 1e-5 of r_list^2 are decided in
 // FP64 as the definition does (the FP32 error is below 2e-6 relative).
+//
+// With at least 3 cells per axis (REL) each chunk is first culled: a candidate
+// farther than the largest r_list from the bounding box of the warp's particles
+// cannot be anyone's neighbour, and the survivors are compacted (about a quarter
+// of the stencil lies outside that reach).  The test yields two bit masks per
+// lane -- r^2 below r_list^2 (1 - band), a neighbour, and below r_list^2 (1 + band)
+// -- so appending a hit is a load of its index and a store, and only the rare
+// candidates between the two go through the FP64 decision.  Hits are appended in
+// candidate order either way, so a row is the same whichever variant built it.
 constexpr int NL_TYPE_SHIFT = 30;
+// a culled candidate is at least this factor beyond the largest r_list^2 (1 + band)
+// from the warp's box, far above the FP32 rounding of the box distance
+constexpr float NL_CULL_MARGIN = 1e-4f;
 
 // fixed-point coordinate of the centre of cell c of nc along an axis
 __device__ __forceinline__ int cell_centre_fixed(int c, int nc) {
   const unsigned long long u = ((2ull * (unsigned long long)c + 1ull) << 32) / (2ull * (unsigned long long)nc);
   return (int)((unsigned int)u ^ 0x80000000u);
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// distance of c from the interval [lo, hi] (0 inside)
+__device__ __forceinline__ float gap_to(float c, float lo, float hi) {
+  return fmaxf(fmaxf(lo - c, c - hi), 0.0f);
+}
+// shift the sign bit of v into the low end of m (candidate k of a chunk of mm
+// ends at bit mm - 1 - k)
+__device__ __forceinline__ unsigned push_sign(unsigned m, float v) {
+  return __funnelshift_l(__float_as_uint(v), m, 1);
 }
 
 // REL: every axis has at least 3 cells, so a candidate's coordinate relative to the
@@ -330,12 +360,18 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   // STAGED: some member of the group may use the staged force path (decided per
   // system below); otherwise none does
   const bool staged = STAGED && s.staged != 0;   // then every axis has >= 4 cells
+  float hi_max = 0.0f;
   for (int k = lane; k < nt * nt; k += 32) {
     const float rl2 = s.pf[k].rl2;
     thr_lo[w][k] = rl2 * (1.0f - NL_BAND);
     thr_hi[w][k] = rl2 * (1.0f + NL_BAND);
     rl2d[w][k] = s.pd[k].rl2;
+    hi_max = fmaxf(hi_max, thr_hi[w][k]);
   }
+  // culling radius^2 of a chunk (the largest r_list, with margin)
+  const float cull2 = warp_max(hi_max) * (1.0f + NL_CULL_MARGIN);
+  // r^2 - hi = (r^2 - lo) - (kappa - 1) lo, kappa = (1 + band) / (1 - band)
+  const float km1 = 2.0f * NL_BAND / (1.0f - NL_BAND);
   const int r = t.first + w;
   const int nc0 = s.nc[0], nc1 = s.nc[1], nc2 = s.nc[2];
   const int lin = s.rank2lin[r];
@@ -400,21 +436,6 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     const int4 qj = qv[j];
     nq = make_int4(qj.x, qj.y, qj.z, j | (qj.w << NL_TYPE_SHIFT));
   };
-  auto stage = [&]() {
-    if (REL) {   // an empty slot sits far away: never within range
-      const bool none = nempty;
-      cxs[w][lane] = none ? 1e18f : (float)min_image_fixed(nq.x, ox) * fs0;
-      cys[w][lane] = none ? 1e18f : (float)min_image_fixed(nq.y, oy) * fs1;
-      czs[w][lane] = none ? 1e18f : (float)min_image_fixed(nq.z, oz) * fs2;
-      cts[w][lane] = (float)(((unsigned)nq.w >> NL_TYPE_SHIFT) & 1u);
-    } else {
-      cxs[w][lane] = __int_as_float(nq.x);
-      cys[w][lane] = __int_as_float(nq.y);
-      czs[w][lane] = __int_as_float(nq.z);
-    }
-    cjs[w][lane] = nq.w;
-    if (STAGED) cand_l[w][lane] = nloc;
-  };
 
   unsigned long long nb_sum = 0;
   for (int ibase = b; ibase < e; ibase += 32) {
@@ -425,87 +446,134 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     const float yi = (float)min_image_fixed(qi.y, oy) * fs1;
     const float zi = (float)min_image_fixed(qi.z, oz) * fs2;
     const float2 nX = make_float2(-xi, -xi), nY = make_float2(-yi, -yi), nZ = make_float2(-zi, -zi);
-    // the test keeps every candidate with r^2 below hi = r_list^2 (1 + band) in a bit
-    // mask (the sign bit of r^2 - hi); the hits are then appended in order, the ones
-    // above r_list^2 (1 - band) after an FP64 decision.  Two types: -hi for a type-0
+    // the bounding box of this pass's particles (REL culling)
+    const float bx0 = warp_min(valid ? xi : 3e38f), bx1 = warp_max(valid ? xi : -3e38f);
+    const float by0 = warp_min(valid ? yi : 3e38f), by1 = warp_max(valid ? yi : -3e38f);
+    const float bz0 = warp_min(valid ? zi : 3e38f), bz1 = warp_max(valid ? zi : -3e38f);
+    // An idle lane gets thresholds -1 (never keeps).  Two types: -lo for a type-0
     // candidate and its change for type 1 in registers; more types read the table.
-    // An idle lane gets hi = -1 (never keeps).
     const int pt = MULTI ? qi.w * nt : 0;
+    const float lo_0 = valid ? thr_lo[w][pt] : -1.0f;
+    const float lo_1 = valid && MULTI ? thr_lo[w][pt + min(1, nt - 1)] : lo_0;
     const float hi0 = valid ? thr_hi[w][pt] : -1.0f;
     const float hi1 = valid && MULTI ? thr_hi[w][pt + min(1, nt - 1)] : hi0;
-    const float2 nh0 = make_float2(-hi0, -hi0), ndh = make_float2(hi0 - hi1, hi0 - hi1);
+    const float2 nl0 = make_float2(-lo_0, -lo_0), ndl = make_float2(lo_0 - lo_1, lo_0 - lo_1);
+    const float2 k2 = make_float2(km1, km1);
     int* __restrict__ nl = s.nl;
     const int stride = s.nl_stride;
     const int i_row = valid ? i : 0;
     int cnt = 0;
     const int m_row = ibase + lane;   // member rank (staged list rows)
     unsigned short* __restrict__ nl16 = reinterpret_cast<unsigned short*>(s.nl);
+    // append candidate k of the chunk (if it is not the particle itself)
+    auto append = [&](int k) {
+      const int cw = cjs[w][k];
+      const int j = cw & ((1 << NL_TYPE_SHIFT) - 1);
+      if (j == i) return;
+      if (staged) nl16[nl16_index(m_row, min(cnt, cap - 1), stride)] = (unsigned short)cand_l[w][k];
+      else nl[nl_index(i_row, min(cnt, cap - 1), stride)] = j;
+      ++cnt;
+    };
     fetch(lane);
     for (int cb = 0; cb < total; cb += 32) {
-      stage();
+      int m = 32;   // candidates in the chunk buffer
+      if (REL) {
+        // relative coordinates; cull against the box and compact the survivors
+        const float qx = (float)min_image_fixed(nq.x, ox) * fs0;
+        const float qy = (float)min_image_fixed(nq.y, oy) * fs1;
+        const float qz = (float)min_image_fixed(nq.z, oz) * fs2;
+        const float gx = gap_to(qx, bx0, bx1), gy = gap_to(qy, by0, by1), gz = gap_to(qz, bz0, bz1);
+        const bool keep = !nempty && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < cull2;
+        const unsigned kb = __ballot_sync(0xffffffffu, keep);
+        m = __popc(kb);
+        const int p = __popc(kb & ((1u << lane) - 1u));
+        if (keep) {
+          cxs[w][p] = qx;
+          cys[w][p] = qy;
+          czs[w][p] = qz;
+          cts[w][p] = (float)(((unsigned)nq.w >> NL_TYPE_SHIFT) & 1u);
+          cjs[w][p] = nq.w;
+          if (STAGED) cand_l[w][p] = nloc;
+        }
+        if (lane == 0 && (m & 1)) {   // the odd chunk's partner slot: never within range
+          cxs[w][m] = 1e18f;
+          cys[w][m] = 1e18f;
+          czs[w][m] = 1e18f;
+          cts[w][m] = 0.0f;
+        }
+      } else {
+        cxs[w][lane] = __int_as_float(nq.x);
+        cys[w][lane] = __int_as_float(nq.y);
+        czs[w][lane] = __int_as_float(nq.z);
+        cjs[w][lane] = nq.w;
+        if (STAGED) cand_l[w][lane] = nloc;
+        m = min(32, total - cb);
+      }
       __syncwarp();
       if (cb + 32 < total) fetch(cb + 32 + lane);   // in flight during the tests
-      unsigned mask = 0;
+      if (m == 0) {
+        __syncwarp();
+        continue;
+      }
+      // masks over the chunk: r^2 below lo (a neighbour) and below hi (a neighbour or
+      // within the band)
+      unsigned mlo = 0, mhi = 0;
       if (REL) {
         // candidates k, k + 1 at once in packed FP32x2
-#pragma unroll
-        for (int k = 0; k < 32; k += 2) {
+        const int mm = (m + 1) & ~1;
+#pragma unroll 4
+        for (int k = 0; k < mm; k += 2) {
           const float2 X = *reinterpret_cast<const float2*>(&cxs[w][k]);
           const float2 Y = *reinterpret_cast<const float2*>(&cys[w][k]);
           const float2 Z = *reinterpret_cast<const float2*>(&czs[w][k]);
-          float2 d;
+          float2 nlo;   // -r_list^2 (1 - band) of each candidate's type pair
           if (!MULTI) {
-            d = nh0;
+            nlo = nl0;
           } else if (two) {
-            d = __ffma2_rn(*reinterpret_cast<const float2*>(&cts[w][k]), ndh, nh0);
+            nlo = __ffma2_rn(*reinterpret_cast<const float2*>(&cts[w][k]), ndl, nl0);
           } else {
             const unsigned t0 = (unsigned)cjs[w][k] >> NL_TYPE_SHIFT;
             const unsigned t1 = (unsigned)cjs[w][k + 1] >> NL_TYPE_SHIFT;
-            d = valid ? make_float2(-thr_hi[w][pt + (t0 & 3)], -thr_hi[w][pt + (t1 & 3)])
-                      : make_float2(1.0f, 1.0f);
+            nlo = valid ? make_float2(-thr_lo[w][pt + (t0 & 3)], -thr_lo[w][pt + (t1 & 3)])
+                        : make_float2(1.0f, 1.0f);
           }
           const float2 dx = __fadd2_rn(X, nX), dy = __fadd2_rn(Y, nY), dz = __fadd2_rn(Z, nZ);
-          d = __ffma2_rn(dx, dx, d);
+          float2 d = __ffma2_rn(dx, dx, nlo);
           d = __ffma2_rn(dy, dy, d);
-          d = __ffma2_rn(dz, dz, d);
-          mask |= ((__float_as_uint(d.x) >> 31) << k) | ((__float_as_uint(d.y) >> 31) << (k + 1));
+          d = __ffma2_rn(dz, dz, d);                  // r^2 - lo
+          const float2 dh = __ffma2_rn(nlo, k2, d);   // r^2 - hi
+          mlo = push_sign(push_sign(mlo, d.x), d.y);
+          mhi = push_sign(push_sign(mhi, dh.x), dh.y);
         }
+        // candidate k to bit k
+        mlo = __brev(mlo) >> (32 - mm);
+        mhi = __brev(mhi) >> (32 - mm);
       } else {
-        const int m = min(32, total - cb);
         for (int k = 0; k < m; ++k) {
           const float dx = (float)min_image_fixed(qi.x, __float_as_int(cxs[w][k])) * fs0;
           const float dy = (float)min_image_fixed(qi.y, __float_as_int(cys[w][k])) * fs1;
           const float dz = (float)min_image_fixed(qi.z, __float_as_int(czs[w][k])) * fs2;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           const unsigned ct = (unsigned)cjs[w][k] >> NL_TYPE_SHIFT;
-          const float hi = !MULTI ? hi0 : two ? ((ct & 1) ? hi1 : hi0)
-                                              : (valid ? thr_hi[w][pt + ct] : -1.0f);
-          mask |= (r2 < hi ? 1u : 0u) << k;
+          const int p = !MULTI ? 0 : two ? (ct & 1) : ct;
+          const float lo = valid ? thr_lo[w][pt + p] : -1.0f;
+          const float hi = valid ? thr_hi[w][pt + p] : -1.0f;
+          mlo |= (r2 < lo ? 1u : 0u) << k;
+          mhi |= (r2 < hi ? 1u : 0u) << k;
         }
       }
-      while (mask) {   // about a tenth of the candidates
-        const int k = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const int cw = cjs[w][k];
-        const int j = cw & ((1 << NL_TYPE_SHIFT) - 1);
-        if (j == i) continue;
-        float r2;
-        if (REL) {
-          const float dx = cxs[w][k] - xi, dy = cys[w][k] - yi, dz = czs[w][k] - zi;
-          r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        } else {
-          const float dx = (float)min_image_fixed(qi.x, __float_as_int(cxs[w][k])) * fs0;
-          const float dy = (float)min_image_fixed(qi.y, __float_as_int(cys[w][k])) * fs1;
-          const float dz = (float)min_image_fixed(qi.z, __float_as_int(czs[w][k])) * fs2;
-          r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      // the hits in candidate order (so the row does not depend on how r^2 was
+      // rounded): below lo a neighbour, between lo and hi the FP64 definition decides
+      while (mhi) {
+        const int k = __ffs(mhi) - 1;
+        mhi &= mhi - 1;
+        if (!((mlo >> k) & 1u)) {
+          const int cw = cjs[w][k];
+          const int j = cw & ((1 << NL_TYPE_SHIFT) - 1);
+          const int p = MULTI ? pt + ((unsigned)cw >> NL_TYPE_SHIFT) : 0;
+          if (j == i || !exact_within(s, i, j, rl2d[w][p])) continue;
         }
-        const int p = MULTI ? pt + ((unsigned)cw >> NL_TYPE_SHIFT) : 0;
-        const bool keep = r2 < thr_lo[w][p] || exact_within(s, i, j, rl2d[w][p]);
-        if (keep) {   // an overflowing row is rebuilt anyway
-          if (staged) nl16[nl16_index(m_row, min(cnt, cap - 1), stride)] = (unsigned short)cand_l[w][k];
-          else nl[nl_index(i_row, min(cnt, cap - 1), stride)] = j;
-          ++cnt;
-        }
+        append(k);
       }
       __syncwarp();
     }
