@@ -372,6 +372,25 @@ const char *gbmd_last_error(void);
 /* GBMD_ABI_VERSION of the loaded library. */
 int gbmd_abi_version(void);
 
+/* Arithmetic throughput probe, a measurement aid with no counterpart in the
+ * paper: the denominator of the roofline of the FP64 force path, which is bound
+ * by the FP64 pipe rather than by memory on this GPU (Section 5 quotes that
+ * path's full-FP64 throughput on a V100).  `kind` selects the operation:
+ *   GBMD_PROBE_DFMA  FP64 fused multiply-add,
+ *   GBMD_PROBE_FFMA  FP32 fused multiply-add,
+ *   GBMD_PROBE_DRCP  FP64 correctly rounded reciprocal (one per pair in the FP64
+ *                    force kernel).
+ * One launch over every SM of the current device (8 blocks of 256 threads per
+ * SM, 8 independent chains per thread, `iters` >= 1 rounds) on `stream`
+ * (cudaStream_t or NULL), after an untimed warm-up launch; *ops receives the
+ * operations executed (a multiply-add counts as one), *ms the CUDA-event time
+ * of the timed launch.  Allocates and frees a small result buffer; synchronises.
+ * GBMD_ERR_BAD_ARG for an unknown kind, iters < 1 or NULL outputs. */
+#define GBMD_PROBE_DFMA 0
+#define GBMD_PROBE_FFMA 1
+#define GBMD_PROBE_DRCP 2
+int gbmd_probe_arith(int32_t kind, int32_t iters, void *stream, double *ops, float *ms);
+
 #ifdef __cplusplus
 }
 #endif

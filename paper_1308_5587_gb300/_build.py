@@ -15,7 +15,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbmd.so")
 SOURCES = ["k_force.cu", "k_force_mie.cu", "k_force_yukawa.cu", "k_force_gauss.cu",
-           "k_lists.cu", "k_tree.cu", "k_step.cu", "gbmd_api.cu"]
+           "k_lists.cu", "k_tree.cu", "k_step.cu", "k_probe.cu", "gbmd_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                 "-diag-suppress", "1444", "-I", INCLUDE]

@@ -1333,6 +1333,15 @@ const char* gbmd_last_error(void) { return g_err.c_str(); }
 
 int gbmd_abi_version(void) { return GBMD_ABI_VERSION; }
 
+int gbmd_probe_arith(int32_t kind, int32_t iters, void* stream, double* ops, float* ms) {
+  if (!ops || !ms) return fail(GBMD_ERR_BAD_ARG, "NULL output");
+  if (kind != GBMD_PROBE_DFMA && kind != GBMD_PROBE_FFMA && kind != GBMD_PROBE_DRCP)
+    return fail(GBMD_ERR_BAD_ARG, "unknown probe kind %d", kind);
+  if (iters < 1) return fail(GBMD_ERR_BAD_ARG, "iters must be >= 1");
+  CK(probe_run(kind, static_cast<cudaStream_t>(stream), iters, ops, ms));
+  return GBMD_OK;
+}
+
 int gbmd_create(const gbmd_desc* d, gbmd_system** out) {
   RET(create_impl(d, out, false));
   int rc = load_state(*out, d->pos, d->vel, d->type, d->image, false, 0);

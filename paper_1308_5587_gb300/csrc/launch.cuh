@@ -83,6 +83,9 @@ KernelCall nlist_export_call(const SysDev* d, const Tile* tiles_p, int ntiles, i
 
 cudaError_t launch(const KernelCall& k, cudaStream_t st);
 
+// arithmetic throughput probe (k_probe.cu): one timed launch over every SM
+cudaError_t probe_run(int kind, cudaStream_t st, int iters, double* ops, float* ms);
+
 // force-kernel variants available (threads per particle)
 bool tpp_supported(int tpp);
 

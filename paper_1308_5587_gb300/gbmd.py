@@ -120,6 +120,8 @@ _SIGS = {
     "gbmd_batch_destroy": (C.c_int, [C.c_void_p]),
     "gbmd_last_error": (C.c_char_p, []),
     "gbmd_abi_version": (C.c_int, []),
+    "gbmd_probe_arith": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_float)]),
 }
 
 
@@ -382,6 +384,19 @@ def gbmd_last_error() -> str:
 
 def gbmd_abi_version() -> int:
     return int(load().gbmd_abi_version())
+
+
+PROBE_KINDS = {"dfma": 0, "ffma": 1, "drcp": 2}
+
+
+def gbmd_probe_arith(kind: str, iters: int, stream=None):
+    """(operations, milliseconds) of one timed probe launch on the current device."""
+    ops = C.c_double(0)
+    ms = C.c_float(0)
+    _check(load().gbmd_probe_arith(PROBE_KINDS.get(kind, kind) if isinstance(kind, str)
+                                   else int(kind), int(iters), _stream_handle(stream),
+                                   C.byref(ops), C.byref(ms)))
+    return ops.value, ms.value
 
 
 # ---- convenience wrappers ----------------------------------------------------------

@@ -131,3 +131,10 @@ def test_footprint_of_the_tree_list(lib):
     tree, k2 = _desc(lib, n=8000, box=24.0, nlist="tree")
     fc, ft = lib.gbmd_footprint_bytes(cell), lib.gbmd_footprint_bytes(tree)
     assert 8000 * 40 < ft - fc < 8000 * 80
+
+
+def test_probe_rejects_bad_arguments_before_any_launch(lib):
+    for kind, iters in ((7, 10), (-1, 10), (0, 0), (1, -5)):
+        with pytest.raises(lib.GbmdError) as e:
+            lib.gbmd_probe_arith(kind, iters)
+        assert e.value.status == "BAD_ARG"
