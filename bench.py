@@ -1,23 +1,28 @@
 #!/usr/bin/env python
 """Benchmark of the LJ MD hot path on GB300 (one JSON line on stdout, rank 0).
 
-Workload (default): the 64,000-particle Lennard-Jones fluid, rho 0.84, T 1.2,
-r_cut 2.5 sigma (energy-shifted), r_buff 0.4, dt 0.005, mixed precision (FP32 pair
-forces, FP64 positions/integration/reductions), seeded synthetic FCC+jitter input.
-A "step" is one velocity-Verlet time step of the whole path: the step kernel (pair
-force, then kick, drift, wrap, shadow and the rebuild check) and the conditional
+Workload (default): the Kob-Andersen 80:20 binary Lennard-Jones mixture,
+N = 10^6, rho 1.2, T 1.0, r_cut 2.5 sigma_ij (energy-shifted), r_buff 0.3, dt 0.005,
+Morton re-sort every 100 steps, mixed precision (FP32 pair forces, FP64
+positions/integration/reductions), seeded synthetic FCC+jitter input.  A "step" is
+one velocity-Verlet time step of the whole path: the step kernel (pair force, then
+kick, drift, wrap, shadow and the rebuild check) and the conditional
 cell-list/neighbour-list rebuild that follows it.
 
 Timing: W untimed warm-up steps, then exactly K steps, each bracketed by CUDA
-events on the system's stream, with a 256 MB write between steps so that every
-step starts with a cold L2 (the working set is smaller than the 129 MB L2).
-A second, shorter pass brackets the force kernel of every step with its own pair
-of events (event nodes inside the step graph) for the roofline figure; those nodes
-add a few microseconds to a step, so the headline pass runs without them.  Clocks are sampled
-with nvidia-smi during the timed region.  The same protocol runs the plain FP64
-path for the "vs FP64 plain path" comparison, and an end-to-end loop through the
-public API with host buffers (upload state, run a chunk of steps, read energy
-and forces back) gives "e2e".
+events on the system's stream.  At 10^6 particles the inputs (the neighbour list
+alone is ~370 MB) exceed the 129 MB L2; smaller workloads write 256 MB between steps
+so that every step starts with a cold L2.  A second, shorter pass brackets the
+force kernel of every step with its own pair of events (event nodes inside the
+step graph) for the roofline figure; those nodes add a few microseconds to a step,
+so the headline pass runs without them.  Clocks are sampled with nvidia-smi during
+the timed region.  An end-to-end loop through the public API with host buffers
+(upload state, run a chunk of steps, read energy and forces back) gives "e2e".
+
+Beside the headline (skipped with --no-sub): the arithmetic peaks measured by the
+library's probe, the LJ 64k fluid in mixed precision and on the plain FP64 path
+with the FP64 pipe roofline ("vs FP64 plain path"), and the 256-replica batched
+ensemble against that plain FP64 single-system loop.
 
 --impl reference times the CPU oracle (FP64, O(N^2)) on this host's cores on a
 bounded sample of the same workload.  Under torchrun each rank runs its own
@@ -347,9 +352,117 @@ def cpu_single_thread(w):
             "sample": f"forces on {m} sampled particles against all {w.n} ({dt:.2f} s)"}
 
 
+def run_system(torch, w, precision, sort_period, stream, dist, local, flush, steps, warmup,
+               force_path="global", autotune=False, tune_cache=None, sample_clocks=True):
+    """Create a system, time `steps` steps (headline pass, no event nodes) and a
+    second pass with the force kernel between event nodes; returns the numbers the
+    lines below are built from."""
+    from paper_1308_5587_gb300 import gbmd
+    s = gbmd.System.from_workload(w, precision=precision, sort_period=sort_period,
+                                  stream=stream.cuda_stream, cuda_device=local,
+                                  force_path=force_path, **system_kw(w))
+    if autotune:
+        s.autotune(tune_cache)
+    clocks = ClockSampler(local) if sample_clocks else None
+    if clocks:
+        clocks.start()
+    step_ms, _, launches = timed_steps(torch, s, steps, warmup, flush, stream, dist)
+    clk = clocks.stop() if clocks else None
+    _, force_ms, _ = timed_steps(torch, s, min(steps, 1000), 3, flush, stream, dist,
+                                 force_events=True)
+    info = s.info()
+    th = s.thermo()
+    s.close()
+    assert math.isfinite(th["pe"]), "non-finite energy"
+    t_local = float(step_ms.sum()) / 1e3
+    t_max = reduce_scalar(dist, t_local, "max")
+    units = reduce_scalar(dist, w.n * steps, "sum")
+    return {"value": units / t_max, "t_max": t_max, "ms_per_step": 1e3 * t_max / steps,
+            "step_ms_mean": float(step_ms.mean()), "force_ms_mean": float(force_ms.mean()),
+            "launches": int(launches), "info": info, "clocks": clk}
+
+
+def hbm_roofline(n, nbar, precision, force_ms, step_ms, info, workload):
+    """Roofline of the step kernel (pair force + integration) in algorithmic bytes
+    per launch: the pair force's own shadow, count and indices (16 + 4 + 4 <n>;
+    neighbour positions come from L1/L2) plus the integration's x, v read and
+    written (96), build shadow read (16) and next shadow written (16), i.e.
+    148 + 4 <n> per particle; FP64 gathers a 32 B own position and also writes its
+    next one.  The pair force alone, as a separate kernel writing its force
+    (36 + 4 <n>), is given beside it on the same kernel time."""
+    peak, peak_kind = measured_peaks()
+    if precision == "mixed":
+        fused = n * (16 + 4 + 4 * nbar + 96 + 16 + 16)
+        k5 = n * (16 + 4 + 4 * nbar + 16)
+    else:
+        fused = n * (32 + 4 + 4 * nbar + 96 + 16 + 16 + 32)
+        k5 = n * (32 + 4 + 4 * nbar + 32)
+    achieved = fused / (force_ms * 1e-3) / 1e9
+    k5_ach = k5 / (force_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(workload, precision),
+            "count": "fused step kernel: N (148 + 4 <n>) B per launch",
+            "kernel": (f"k_force_staged<{precision}>" if info["force_path"] == 1 else
+                       f"k_force<{precision}> (step mode) tpp={info['threads_per_particle']} "
+                       f"block={info['force_block']}"),
+            "alg_bytes_per_launch": int(fused), "mean_neighbors": round(nbar, 2),
+            "force_ms_mean": round(force_ms, 5), "peak_kind": f"of {peak_kind}",
+            "force_share_of_step": round(force_ms / step_ms, 3),
+            "k5_only": {"count": "pair force alone: N (36 + 4 <n>) B per launch",
+                        "alg_bytes_per_launch": int(k5), "achieved": round(k5_ach, 1),
+                        "frac": round(k5_ach / peak, 4)}}
+
+
+def probe_peaks(torch, local):
+    """Arithmetic peaks measured here by the library's probe: FP64 FMA, FP32 FMA and
+    the FP64 reciprocal, per second and per SM per clock at the sampled SM clock."""
+    from paper_1308_5587_gb300 import gbmd
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    clocks = ClockSampler(local)
+    clocks.start()
+    out = {}
+    for kind, iters in (("dfma", 2048), ("ffma", 65536), ("drcp", 512)):
+        best = None
+        for _ in range(3):
+            ops, ms = gbmd.gbmd_probe_arith(kind, iters)
+            rate = ops / (ms * 1e-3)
+            best = rate if best is None else max(best, rate)
+        out[kind] = {"ops_per_s": best}
+    clk = clocks.stop()
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz")
+    for v in out.values():
+        v["per_sm_per_clock"] = round(v["ops_per_s"] / (sms * mhz * 1e6), 3) if mhz else None
+    out["sms"] = sms
+    out["clocks"] = clk
+    out["drcp_in_dfma_slots"] = round(out["dfma"]["ops_per_s"] / out["drcp"]["ops_per_s"], 2)
+    return out
+
+
+def fp64_roofline(n, nbar, force_ms, peaks, r_cut, r_list):
+    """Roofline of the FP64 step kernel against the measured FP64 FMA rate.  FP64
+    operations (each add, multiply or fused multiply-add counts one) from the
+    kernel's arithmetic: per listed pair the displacement (3) and r^2 (3); per pair
+    inside r_cut one reciprocal (counted as the DFMA slots it takes, measured by the
+    probe), r^-6 (2), the force factor (3) and the three accumulations (3); per
+    particle the integration's kicks, drifts, rounding and FP64 shadow (13).  The
+    share of listed pairs inside r_cut is the uniform-fluid estimate
+    (r_cut / r_list)^3."""
+    rcp = peaks["drcp_in_dfma_slots"]
+    f_cut = (r_cut / r_list) ** 3
+    per_pair = 6 + f_cut * (8 + rcp)
+    ops = n * (nbar * per_pair + 13)
+    achieved = ops / (force_ms * 1e-3)
+    peak = peaks["dfma"]["ops_per_s"]
+    return {"bound": "fp64", "achieved": round(achieved / 1e12, 4), "peak": round(peak / 1e12, 4),
+            "unit": "T FP64 ops/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "k_force<fp64> (step mode)", "ops_per_launch": int(ops),
+            "ops_per_listed_pair": round(per_pair, 2), "share_inside_rcut": round(f_cut, 3),
+            "peak_kind": "of measured (gbmd_probe_arith DFMA, this run)"}
+
+
 def gpu_arm(args):
     import torch
-    from paper_1308_5587_gb300 import _build, gbmd
+    from paper_1308_5587_gb300 import _build
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dist = dist_init(world)
@@ -358,66 +471,28 @@ def gpu_arm(args):
     w, precision, sort_period, wdesc = make_workload(args.workload, rank)
     n = w.n
     flush = None
-    if args.workload != "ka1m":     # working set < L2: write 256 MB between steps
+    if n * 500 < 256e6:     # working set < L2: write 256 MB between steps
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    s = gbmd.System.from_workload(w, precision=precision, sort_period=sort_period,
-                                  stream=stream.cuda_stream, cuda_device=local,
-                                  force_path=args.force_path, **system_kw(w))
-    if args.autotune:
-        s.autotune(args.tune_cache)
-    clocks = ClockSampler(local)
-    clocks.start()
-    step_ms, _, launches = timed_steps(torch, s, args.steps, args.warmup, flush, stream, dist)
-    clk = clocks.stop()
-    # second pass for the roofline: the force kernel between event nodes
-    _, force_ms, _ = timed_steps(torch, s, min(args.steps, 1000), 3, flush, stream, dist,
-                                 force_events=True)
-    info = s.info()
-    th = s.thermo()
-    s.close()
-    assert math.isfinite(th["pe"]), "non-finite energy"
-
-    t_local = float(step_ms.sum()) / 1e3
-    t_max = reduce_scalar(dist, t_local, "max")
-    units = reduce_scalar(dist, n * args.steps, "sum")
-    value = units / t_max
-    ms_per_step = 1e3 * t_max / args.steps
-
-    # roofline of the dominant kernel, the step kernel (pair force + integrate), in
-    # algorithmic bytes per launch and particle: the pair force's own shadow, count
-    # and indices (16 + 4 + 4 <n>; neighbour positions come from L1/L2) plus the
-    # integration's x, v read and written (96), build shadow read (16) and next
-    # shadow written (16); FP64 gathers a 32 B position and also writes its next one
+    r = run_system(torch, w, precision, sort_period, stream, dist, local, flush, args.steps,
+                   args.warmup, args.force_path, args.autotune, args.tune_cache)
+    info = r["info"]
+    value = r["value"]
     nbar = info["neighbors_total"] / n
-    if precision == "mixed":
-        alg_bytes = n * (16 + 4 + 4 * nbar + 96 + 16 + 16)
-    else:
-        alg_bytes = n * (32 + 4 + 4 * nbar + 96 + 16 + 16 + 32)
-    peak, peak_kind = measured_peaks()
-    f_mean = float(force_ms.mean())
-    achieved = alg_bytes / (f_mean * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": recorded_traffic(args.workload, precision),
-                "kernel": (f"k_force_staged<{precision}>" if info["force_path"] == 1 else
-                           f"k_force<{precision}> tpp={info['threads_per_particle']} "
-                           f"block={info['force_block']}"),
-                "alg_bytes_per_launch": int(alg_bytes), "mean_neighbors": round(nbar, 2),
-                "force_ms_mean": round(f_mean, 5), "peak_kind": f"of {peak_kind}",
-                "force_share_of_step": round(f_mean / float(step_ms.mean()), 3)}
-
+    roofline = hbm_roofline(n, nbar, precision, r["force_ms_mean"], r["step_ms_mean"], info,
+                            args.workload)
     # second line: the whole step -- the step kernel plus the amortised rebuild, which
     # writes the list (4 <n>) and ~60 B of cell-list and count traffic per particle
+    peak, peak_kind = measured_peaks()
     reb = info["n_rebuilds"] / max(info["step"], 1)
-    step_bytes = alg_bytes + n * reb * (60 + 4 * nbar)
-    step_achieved = step_bytes / (float(step_ms.mean()) * 1e-3) / 1e9
+    step_bytes = roofline["alg_bytes_per_launch"] + n * reb * (60 + 4 * nbar)
+    step_achieved = step_bytes / (r["step_ms_mean"] * 1e-3) / 1e9
     roofline_step = {"bound": "hbm", "achieved": round(step_achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(step_achieved / peak, 4),
                      "alg_bytes_per_step": int(step_bytes), "peak_kind": f"of {peak_kind}"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
            "scaling": "weak",
            "vs_baseline": (value / PAPER_V100_FP64 if args.workload == "paper64k" else None),
            "dtype": "f32 pair forces + f64 integration" if precision == "mixed" else "f64",
@@ -433,27 +508,9 @@ def gpu_arm(args):
                       "force_block": info["force_block"], "nlist_capacity": info["nlist_capacity"],
                       "force_path": "staged" if info["force_path"] == 1 else "global",
                       "sort_period": sort_period},
-           "tps": args.steps / t_max, "roofline": roofline, "roofline_step": roofline_step,
-           "clocks": clk,
-           "gpu_launches": int(launches),
-           "rebuilds_per_step": None}
-    out["rebuilds_per_step"] = round(info["n_rebuilds"] / max(info["step"], 1), 4)
-
-    # plain FP64 path on the same workload, same protocol
-    if not args.no_fp64 and precision == "mixed" and args.workload == "lj64k":
-        s64 = gbmd.System.from_workload(w, precision="fp64", sort_period=sort_period,
-                                        stream=stream.cuda_stream, cuda_device=local)
-        k64 = max(20, args.steps // 20)
-        st64, _, _ = timed_steps(torch, s64, k64, max(3, args.warmup // 20), flush, stream, dist)
-        _, f64, _ = timed_steps(torch, s64, min(k64, 100), 3, flush, stream, dist,
-                                force_events=True)
-        s64.close()
-        t64 = reduce_scalar(dist, float(st64.sum()) / 1e3, "max")
-        v64 = reduce_scalar(dist, n * k64, "sum") / t64
-        out["fp64_plain"] = {"value": v64, "unit": UNIT, "steps": k64,
-                             "ms_per_step": 1e3 * t64 / k64,
-                             "force_ms_mean": round(float(f64.mean()), 4),
-                             "mixed_over_fp64": round(value / v64, 2)}
+           "tps": args.steps / r["t_max"], "roofline": roofline, "roofline_step": roofline_step,
+           "clocks": r["clocks"], "gpu_launches": r["launches"],
+           "rebuilds_per_step": round(reb, 4)}
 
     # end to end through the public API with host buffers
     chunk = 100
@@ -466,6 +523,9 @@ def gpu_arm(args):
                   "loop": f"{iters} x (set_state from pinned host -> {chunk} steps -> "
                           "thermo + forces to pinned host)"}
 
+    if not args.no_sub and world == 1:
+        sub_records(torch, args, out, stream, dist, local)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, rank)
         out["cpu_baseline"]["single_thread"] = cpu_single_thread(w)
@@ -473,6 +533,42 @@ def gpu_arm(args):
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def sub_records(torch, args, out, stream, dist, local):
+    """Beside the headline: the arithmetic peaks, the LJ 64k fluid in mixed precision
+    and on the plain FP64 path (with the FP64 roofline), and the batched ensemble
+    against that plain FP64 single-system loop."""
+    from paper_1308_5587_gb300 import workloads as wl
+    peaks = probe_peaks(torch, local)
+    out["peaks_probe"] = peaks
+    w64 = wl.lj_64k(wl.BASE_SEED)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    k = max(20, min(args.steps, 200))
+    mixed = run_system(torch, w64, "mixed", 100, stream, dist, local, flush, k, 5,
+                       sample_clocks=False)
+    fp64 = run_system(torch, w64, "fp64", 100, stream, dist, local, flush, k, 5,
+                      sample_clocks=False)
+    nbar64 = fp64["info"]["neighbors_total"] / w64.n
+    out["lj64k"] = {
+        "workload": "lj_fluid N=64000 rho=0.84 T=1.2 rc=2.5 shifted rbuff=0.4 dt=0.005",
+        "steps": k, "l2": "flushed between steps (256 MB write)",
+        "mixed": {"value": mixed["value"], "unit": UNIT, "ms_per_step": mixed["ms_per_step"],
+                  "roofline": hbm_roofline(w64.n, mixed["info"]["neighbors_total"] / w64.n,
+                                           "mixed", mixed["force_ms_mean"],
+                                           mixed["step_ms_mean"], mixed["info"], "lj64k")},
+        "fp64_plain": {"value": fp64["value"], "unit": UNIT, "ms_per_step": fp64["ms_per_step"],
+                       "force_ms_mean": round(fp64["force_ms_mean"], 5),
+                       "roofline": fp64_roofline(w64.n, nbar64, fp64["force_ms_mean"], peaks,
+                                                 2.5, 2.5 + w64.r_buff)},
+        "mixed_over_fp64": round(mixed["value"] / fp64["value"], 2)}
+    torch.cuda.synchronize()
+    del flush
+    b = run_batch(torch, args.replicas, 50, 5, stream, dist, local, autotune=False)
+    b["fp64_single_system_loop"] = {"value": fp64["value"], "unit": UNIT,
+                                    "what": "plain FP64 path, LJ 64k single system (above)"}
+    b["batched_over_fp64_loop"] = round(b["value"] / fp64["value"], 2)
+    out["batched"] = b
 
 
 # ---------------------------------------------------------------------------
@@ -498,15 +594,12 @@ class _BatchStepper:
         self.systems[0].set_force_events(a, b)   # events live in the batch's step graph
 
 
-def batch_arm(args):
-    import torch
-    from paper_1308_5587_gb300 import _build, gbmd, workloads as wl
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = dist_init(world)
-    _build.build()
-    stream = torch.cuda.current_stream()
-    params = wl.replica_params(args.replicas, seed=wl.BASE_SEED + 1000 * rank)
+def run_batch(torch, replicas, steps, warmup, stream, dist, local, autotune=True):
+    """The batched ensemble (replicas of uneven size in one batch), timed like a
+    single system; returns a record for the JSON line."""
+    from paper_1308_5587_gb300 import gbmd, workloads as wl
+    rank, _, _ = dist_env()
+    params = wl.replica_params(replicas, seed=wl.BASE_SEED + 1000 * rank)
     ws = [wl.replica(*p) for p in params]
     b = gbmd.Batch("mixed", stream=stream.cuda_stream, cuda_device=local)
     systems = [gbmd.System.from_workload(w, precision="mixed", sort_period=100,
@@ -514,50 +607,69 @@ def batch_arm(args):
                for w in ws]
     for x in systems:
         b.add(x)
-    if not args.no_autotune:
+    if autotune:
         b.autotune(None)
     n = sum(w.n for w in ws)
     clocks = ClockSampler(local)
     clocks.start()
     stepper = _BatchStepper(b, systems)
-    step_ms, _, launches = timed_steps(torch, stepper, args.steps, args.warmup, None, stream, dist)
+    step_ms, _, launches = timed_steps(torch, stepper, steps, warmup, None, stream, dist)
     clk = clocks.stop()
-    _, force_ms, _ = timed_steps(torch, stepper, min(args.steps, 500), 3, None, stream, dist,
+    _, force_ms, _ = timed_steps(torch, stepper, min(steps, 500), 3, None, stream, dist,
                                  force_events=True)
     infos = [x.info() for x in systems]
     tune = (infos[0]["threads_per_particle"], infos[0]["force_block"])
     th = [x.thermo() for x in systems[:4]]
     assert all(math.isfinite(t["pe"]) for t in th)
     t_max = reduce_scalar(dist, float(step_ms.sum()) / 1e3, "max")
-    value = reduce_scalar(dist, n * args.steps, "sum") / t_max
+    value = reduce_scalar(dist, n * steps, "sum") / t_max
     alg_bytes = sum(i["n"] * (16 + 4 + 96 + 16 + 16) + 4 * i["neighbors_total"] for i in infos)
     peak, peak_kind = measured_peaks()
     f_mean = float(force_ms.mean())
     achieved = alg_bytes / (f_mean * 1e-3) / 1e9
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32 pair forces + f64 integration",
-           "data": "synthetic (seeded FCC + jitter, Maxwell-Boltzmann; no dataset)",
-           "config": {"workload": f"batched ensemble: {len(ws)} LJ replicas, N_k log-uniform "
-                                  "[500, 20000], rho U(0.7, 0.9), T U(0.8, 1.5), rc 2.5, "
-                                  "rbuff 0.4, dt 0.005, mixed",
-                      "n": n, "replicas": len(ws), "precision": "mixed",
-                      "parallelism": f"replicas x{world}" if world > 1 else "one batch",
-                      "l2": "inputs larger than L2", "timed_iteration":
-                          "one step of every replica (one single-step CUDA graph)",
-                      "threads_per_particle": tune[0], "force_block": tune[1]},
-           "tps": args.steps / t_max,
-           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                        "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                        "kernel": "k_force<mixed> over all replicas",
-                        "alg_bytes_per_launch": int(alg_bytes), "force_ms_mean": round(f_mean, 5),
-                        "peak_kind": f"of {peak_kind}"},
-           "clocks": clk, "gpu_launches": int(launches),
-           "e2e": None}
     for slot in list(b.members):
         b.remove(slot).close()
     b.close()
+    return {"value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": 1e3 * t_max / steps, "tps": steps / t_max,
+            "workload": f"batched ensemble: {len(ws)} LJ replicas, N_k log-uniform "
+                        "[500, 20000], rho U(0.7, 0.9), T U(0.8, 1.5), rc 2.5, "
+                        "rbuff 0.4, dt 0.005, mixed",
+            "n": n, "replicas": len(ws), "threads_per_particle": tune[0],
+            "force_block": tune[1], "autotuned": bool(autotune),
+            "l2": "inputs larger than L2",
+            "timed_iteration": "one step of every replica (one single-step CUDA graph)",
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "k_force<mixed> (step mode) over all replicas",
+                         "alg_bytes_per_launch": int(alg_bytes),
+                         "force_ms_mean": round(f_mean, 5), "peak_kind": f"of {peak_kind}"},
+            "clocks": clk, "gpu_launches": int(launches)}
+
+
+def batch_arm(args):
+    import torch
+    from paper_1308_5587_gb300 import _build
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world)
+    _build.build()
+    stream = torch.cuda.current_stream()
+    r = run_batch(torch, args.replicas, args.steps, args.warmup, stream, dist, local,
+                  autotune=not args.no_autotune)
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 pair forces + f64 integration",
+           "data": "synthetic (seeded FCC + jitter, Maxwell-Boltzmann; no dataset)",
+           "config": {"workload": r["workload"], "n": r["n"], "replicas": r["replicas"],
+                      "precision": "mixed",
+                      "parallelism": f"replicas x{world}" if world > 1 else "one batch",
+                      "l2": r["l2"], "timed_iteration": r["timed_iteration"],
+                      "threads_per_particle": r["threads_per_particle"],
+                      "force_block": r["force_block"]},
+           "tps": r["tps"], "roofline": r["roofline"], "clocks": r["clocks"],
+           "gpu_launches": r["gpu_launches"], "e2e": None}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -683,6 +795,18 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def peaks_arm(args):
+    import torch
+    from paper_1308_5587_gb300 import _build
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    p = probe_peaks(torch, local)
+    if rank == 0:
+        print(json.dumps({"peaks_probe": p, "device": torch.cuda.get_device_name(local)}),
+              flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -692,7 +816,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k", "paper64k", "paper64k_mixed",
                                            *POTENTIAL_WORKLOADS, *COLLOID_WORKLOADS,
                                            "batch", "serve"],
-                    default="lj64k")
+                    default="ka1m")
     ap.add_argument("--replicas", type=int, default=256, help="batch workload: replicas")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: fixed tuning")
     ap.add_argument("--requests", type=int, default=200, help="serve workload: trace length")
@@ -705,7 +829,12 @@ def main(argv=None):
     ap.add_argument("--force-path", choices=["global", "staged"], default="global",
                     help="neighbour gather through L1/L2 by 32-bit index (default) or "
                          "from a shared-memory window by 16-bit index")
-    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-sub", "--no-fp64", dest="no_sub", action="store_true",
+                    help="skip the sub-records beside the headline (arithmetic peaks, LJ 64k "
+                         "mixed and plain FP64, batched ensemble)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="only run the arithmetic probe (FP64 / FP32 FMA, FP64 reciprocal) and "
+                         "print its rates")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the same kernels directly instead of through CUDA graphs "
@@ -717,6 +846,8 @@ def main(argv=None):
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         reference_arm(args)
+    elif args.peaks:
+        peaks_arm(args)
     elif args.workload == "batch":
         batch_arm(args)
     elif args.workload == "serve":
