@@ -353,10 +353,10 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   // the chunk of 32 candidates, one array per component so that candidates k and
   // k + 1 load as one FP32x2 operand: x, y, z (relative to the cell centre; raw
   // fixed point without REL), the type as 0/1, and j | type << 30
-  __shared__ __align__(8) float cxs[CELLS_PER_TILE][32], cys[CELLS_PER_TILE][32],
-      czs[CELLS_PER_TILE][32], cts[CELLS_PER_TILE][32];
-  __shared__ int cjs[CELLS_PER_TILE][32];
-  __shared__ int cand_l[STAGED ? CELLS_PER_TILE : 1][32];   // window-local index
+  __shared__ __align__(8) float cxs[CELLS_PER_TILE][64], cys[CELLS_PER_TILE][64],
+      czs[CELLS_PER_TILE][64], cts[CELLS_PER_TILE][64];
+  __shared__ int cjs[CELLS_PER_TILE][64];
+  __shared__ int cand_l[STAGED ? CELLS_PER_TILE : 1][64];   // window-local index
   // STAGED: some member of the group may use the staged force path (decided per
   // system below); otherwise none does
   const bool staged = STAGED && s.staged != 0;   // then every axis has >= 4 cells
@@ -384,6 +384,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   const int lo1 = nc1 >= 3 ? -1 : 0, n1 = nc1 >= 3 ? 3 : nc1;
   const int lo2 = nc2 >= 3 ? -1 : 0, n2 = nc2 >= 3 ? 3 : nc2;
   const int nsc = n0 * n1 * n2;   // <= 27
+  const int own_sc = -lo0 + n0 * (-lo1 + n1 * -lo2);   // the cell's own stencil slot
   int sc_start = 0, sc_cnt = 0, sc_woff = 0;
   if (lane < nsc) {
     const int dx = lo0 + lane % n0, dy = lo1 + (lane / n0) % n1, dz = lo2 + lane / (n0 * n1);
@@ -455,85 +456,77 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     const int pt = MULTI ? qi.w * nt : 0;
     const float lo_0 = valid ? thr_lo[w][pt] : -1.0f;
     const float lo_1 = valid && MULTI ? thr_lo[w][pt + min(1, nt - 1)] : lo_0;
-    const float hi0 = valid ? thr_hi[w][pt] : -1.0f;
-    const float hi1 = valid && MULTI ? thr_hi[w][pt + min(1, nt - 1)] : hi0;
     const float2 nl0 = make_float2(-lo_0, -lo_0), ndl = make_float2(lo_0 - lo_1, lo_0 - lo_1);
     const float2 k2 = make_float2(km1, km1);
-    int* __restrict__ nl = s.nl;
     const int stride = s.nl_stride;
     const int i_row = valid ? i : 0;
     int cnt = 0;
+    // the row's next ELL4 entry: entry k at row + (k / 4) * 4 stride + k % 4
+    int* wp = s.nl + (size_t)i_row * 4;
+    const size_t step4 = (size_t)stride * 4 - 3;
     const int m_row = ibase + lane;   // member rank (staged list rows)
     unsigned short* __restrict__ nl16 = reinterpret_cast<unsigned short*>(s.nl);
-    // append candidate k of the chunk (if it is not the particle itself)
-    auto append = [&](int k) {
-      const int cw = cjs[w][k];
-      const int j = cw & ((1 << NL_TYPE_SHIFT) - 1);
-      if (j == i) return;
-      if (staged) nl16[nl16_index(m_row, min(cnt, cap - 1), stride)] = (unsigned short)cand_l[w][k];
-      else nl[nl_index(i_row, min(cnt, cap - 1), stride)] = j;
-      ++cnt;
-    };
-    fetch(lane);
-    for (int cb = 0; cb < total; cb += 32) {
-      int m = 32;   // candidates in the chunk buffer
-      if (REL) {
-        // relative coordinates; cull against the box and compact the survivors
-        const float qx = (float)min_image_fixed(nq.x, ox) * fs0;
-        const float qy = (float)min_image_fixed(nq.y, oy) * fs1;
-        const float qz = (float)min_image_fixed(nq.z, oz) * fs2;
-        const float gx = gap_to(qx, bx0, bx1), gy = gap_to(qy, by0, by1), gz = gap_to(qz, bz0, bz1);
-        const bool keep = !nempty && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < cull2;
-        const unsigned kb = __ballot_sync(0xffffffffu, keep);
-        m = __popc(kb);
-        const int p = __popc(kb & ((1u << lane) - 1u));
-        if (keep) {
-          cxs[w][p] = qx;
-          cys[w][p] = qy;
-          czs[w][p] = qz;
-          cts[w][p] = (float)(((unsigned)nq.w >> NL_TYPE_SHIFT) & 1u);
-          cjs[w][p] = nq.w;
-          if (STAGED) cand_l[w][p] = nloc;
-        }
-        if (lane == 0 && (m & 1)) {   // the odd chunk's partner slot: never within range
-          cxs[w][m] = 1e18f;
-          cys[w][m] = 1e18f;
-          czs[w][m] = 1e18f;
-          cts[w][m] = 0.0f;
+    // the particle's own place in the candidate stream (its cell is stencil cell
+    // own_sc; a pass covers members ibase .. ibase + 31 of that cell)
+    const int self_pos = __shfl_sync(0xffffffffu, excl, own_sc) + (ibase - b) + lane;
+
+    // Hits of the 32 candidates at ring slots hb .. hb + 31: candidate k at bit 31 - k
+    // of mlo (r^2 below lo: a neighbour) and mhi (below hi: a neighbour or within the
+    // band).  The band is decided in FP64 first; then the hits are appended in
+    // candidate order (the row does not depend on how r^2 was rounded).  Entries
+    // past the capacity are counted, not stored.
+    auto append_hits = [&](unsigned mlo, unsigned mhi, int hb) {
+      unsigned band = mhi & ~mlo;
+      while (band) {
+        const int k = __clz(band);
+        band &= 0x7fffffffu >> k;
+        const int cw = cjs[w][hb + k];
+        const int j = cw & ((1 << NL_TYPE_SHIFT) - 1);
+        const int p = MULTI ? pt + ((unsigned)cw >> NL_TYPE_SHIFT) : 0;
+        if (!exact_within(s, i, j, rl2d[w][p])) mhi &= ~(0x80000000u >> k);
+      }
+      if (!staged) {
+        const int* __restrict__ cj = &cjs[w][hb];
+        while (mhi) {
+          const int k = __clz(mhi);
+          mhi &= 0x7fffffffu >> k;
+          const int j = cj[k] & ((1 << NL_TYPE_SHIFT) - 1);
+          if (cnt < cap) *wp = j;
+          ++cnt;
+          wp += (cnt & 3) ? 1 : step4;
         }
       } else {
-        cxs[w][lane] = __int_as_float(nq.x);
-        cys[w][lane] = __int_as_float(nq.y);
-        czs[w][lane] = __int_as_float(nq.z);
-        cjs[w][lane] = nq.w;
-        if (STAGED) cand_l[w][lane] = nloc;
-        m = min(32, total - cb);
+        while (mhi) {
+          const int k = __clz(mhi);
+          mhi &= 0x7fffffffu >> k;
+          if (cnt < cap) nl16[nl16_index(m_row, cnt, stride)] = (unsigned short)cand_l[w][hb + k];
+          ++cnt;
+        }
       }
-      __syncwarp();
-      if (cb + 32 < total) fetch(cb + 32 + lane);   // in flight during the tests
-      if (m == 0) {
-        __syncwarp();
-        continue;
-      }
-      // masks over the chunk: r^2 below lo (a neighbour) and below hi (a neighbour or
-      // within the band)
-      unsigned mlo = 0, mhi = 0;
-      if (REL) {
-        // candidates k, k + 1 at once in packed FP32x2
-        const int mm = (m + 1) & ~1;
-#pragma unroll 4
-        for (int k = 0; k < mm; k += 2) {
-          const float2 X = *reinterpret_cast<const float2*>(&cxs[w][k]);
-          const float2 Y = *reinterpret_cast<const float2*>(&cys[w][k]);
-          const float2 Z = *reinterpret_cast<const float2*>(&czs[w][k]);
+    };
+
+    fetch(lane);
+    if (REL) {
+      // Kept candidates go into a ring of 64 slots in stream order; every time 32
+      // are waiting they are tested together (a full, unrolled chunk), so culling
+      // saves tests and not only stores.  The particle's own candidate is always
+      // kept (it lies in the box); selfabs is its ring position.
+      int fill = 0, tested = 0, selfabs = -1;
+      auto test32 = [&](int hb) {
+        unsigned mlo = 0, mhi = 0;
+#pragma unroll
+        for (int k = 0; k < 32; k += 2) {
+          const float2 X = *reinterpret_cast<const float2*>(&cxs[w][hb + k]);
+          const float2 Y = *reinterpret_cast<const float2*>(&cys[w][hb + k]);
+          const float2 Z = *reinterpret_cast<const float2*>(&czs[w][hb + k]);
           float2 nlo;   // -r_list^2 (1 - band) of each candidate's type pair
           if (!MULTI) {
             nlo = nl0;
           } else if (two) {
-            nlo = __ffma2_rn(*reinterpret_cast<const float2*>(&cts[w][k]), ndl, nl0);
+            nlo = __ffma2_rn(*reinterpret_cast<const float2*>(&cts[w][hb + k]), ndl, nl0);
           } else {
-            const unsigned t0 = (unsigned)cjs[w][k] >> NL_TYPE_SHIFT;
-            const unsigned t1 = (unsigned)cjs[w][k + 1] >> NL_TYPE_SHIFT;
+            const unsigned t0 = (unsigned)cjs[w][hb + k] >> NL_TYPE_SHIFT;
+            const unsigned t1 = (unsigned)cjs[w][hb + k + 1] >> NL_TYPE_SHIFT;
             nlo = valid ? make_float2(-thr_lo[w][pt + (t0 & 3)], -thr_lo[w][pt + (t1 & 3)])
                         : make_float2(1.0f, 1.0f);
           }
@@ -545,37 +538,90 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
           mlo = push_sign(push_sign(mlo, d.x), d.y);
           mhi = push_sign(push_sign(mhi, dh.x), dh.y);
         }
-        // candidate k to bit k
-        mlo = __brev(mlo) >> (32 - mm);
-        mhi = __brev(mhi) >> (32 - mm);
-      } else {
-        for (int k = 0; k < m; ++k) {
-          const float dx = (float)min_image_fixed(qi.x, __float_as_int(cxs[w][k])) * fs0;
-          const float dy = (float)min_image_fixed(qi.y, __float_as_int(cys[w][k])) * fs1;
-          const float dz = (float)min_image_fixed(qi.z, __float_as_int(czs[w][k])) * fs2;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const unsigned ct = (unsigned)cjs[w][k] >> NL_TYPE_SHIFT;
-          const int p = !MULTI ? 0 : two ? (ct & 1) : ct;
+        const int rs = selfabs - tested;
+        if (rs >= 0 && rs < 32) {
+          mlo &= ~(0x80000000u >> rs);
+          mhi &= ~(0x80000000u >> rs);
+        }
+        append_hits(mlo, mhi, hb);
+      };
+      for (int cb = 0; cb < total; cb += 32) {
+        // relative coordinates; cull against the box and compact the survivors
+        const float qx = (float)min_image_fixed(nq.x, ox) * fs0;
+        const float qy = (float)min_image_fixed(nq.y, oy) * fs1;
+        const float qz = (float)min_image_fixed(nq.z, oz) * fs2;
+        const float gx = gap_to(qx, bx0, bx1), gy = gap_to(qy, by0, by1), gz = gap_to(qz, bz0, bz1);
+        const bool keep = !nempty && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < cull2;
+        const unsigned kb = __ballot_sync(0xffffffffu, keep);
+        const int p = fill + __popc(kb & ((1u << lane) - 1u));
+        if (keep) {
+          const int sl = p & 63;
+          cxs[w][sl] = qx;
+          cys[w][sl] = qy;
+          czs[w][sl] = qz;
+          cts[w][sl] = (float)(((unsigned)nq.w >> NL_TYPE_SHIFT) & 1u);
+          cjs[w][sl] = nq.w;
+          if (STAGED) cand_l[w][sl] = nloc;
+        }
+        const int rs = self_pos - cb;
+        if (rs >= 0 && rs < 32) selfabs = fill + __popc(kb & ((1u << rs) - 1u));
+        fill += __popc(kb);
+        __syncwarp();
+        if (cb + 32 < total) fetch(cb + 32 + lane);   // in flight during the tests
+        if (fill - tested >= 32) {
+          test32(tested & 63);
+          tested += 32;
+        }
+        __syncwarp();
+      }
+      if (fill > tested) {   // the last, partial chunk: pad it with far-away slots
+        if (lane >= fill - tested) {
+          const int sl = (tested + lane) & 63;
+          cxs[w][sl] = 1e18f;
+          cys[w][sl] = 1e18f;
+          czs[w][sl] = 1e18f;
+          cts[w][sl] = 0.0f;
+          cjs[w][sl] = 0;
+        }
+        __syncwarp();
+        test32(tested & 63);
+        __syncwarp();
+      }
+    } else {
+      for (int cb = 0; cb < total; cb += 32) {
+        cxs[w][lane] = __int_as_float(nq.x);
+        cys[w][lane] = __int_as_float(nq.y);
+        czs[w][lane] = __int_as_float(nq.z);
+        cjs[w][lane] = nq.w;
+        if (STAGED) cand_l[w][lane] = nloc;
+        const int m = min(32, total - cb);
+        __syncwarp();
+        if (cb + 32 < total) fetch(cb + 32 + lane);   // in flight during the tests
+        unsigned mlo = 0, mhi = 0;
+        for (int k = 0; k < 32; ++k) {
+          float r2 = 3e38f;
+          int p = 0;
+          if (k < m) {
+            const float dx = (float)min_image_fixed(qi.x, __float_as_int(cxs[w][k])) * fs0;
+            const float dy = (float)min_image_fixed(qi.y, __float_as_int(cys[w][k])) * fs1;
+            const float dz = (float)min_image_fixed(qi.z, __float_as_int(czs[w][k])) * fs2;
+            r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const unsigned ct = (unsigned)cjs[w][k] >> NL_TYPE_SHIFT;
+            p = !MULTI ? 0 : two ? (int)(ct & 1) : (int)ct;
+          }
           const float lo = valid ? thr_lo[w][pt + p] : -1.0f;
           const float hi = valid ? thr_hi[w][pt + p] : -1.0f;
-          mlo |= (r2 < lo ? 1u : 0u) << k;
-          mhi |= (r2 < hi ? 1u : 0u) << k;
+          mlo = (mlo << 1) | (r2 < lo ? 1u : 0u);
+          mhi = (mhi << 1) | (r2 < hi ? 1u : 0u);
         }
-      }
-      // the hits in candidate order (so the row does not depend on how r^2 was
-      // rounded): below lo a neighbour, between lo and hi the FP64 definition decides
-      while (mhi) {
-        const int k = __ffs(mhi) - 1;
-        mhi &= mhi - 1;
-        if (!((mlo >> k) & 1u)) {
-          const int cw = cjs[w][k];
-          const int j = cw & ((1 << NL_TYPE_SHIFT) - 1);
-          const int p = MULTI ? pt + ((unsigned)cw >> NL_TYPE_SHIFT) : 0;
-          if (j == i || !exact_within(s, i, j, rl2d[w][p])) continue;
+        const int rs = self_pos - cb;
+        if (rs >= 0 && rs < 32) {
+          mlo &= ~(0x80000000u >> rs);
+          mhi &= ~(0x80000000u >> rs);
         }
-        append(k);
+        append_hits(mlo, mhi, 0);
+        __syncwarp();
       }
-      __syncwarp();
     }
     if (valid) {
       s.nn[i] = cnt < cap ? cnt : cap;
