@@ -154,6 +154,9 @@ def make_workload(name: str, rank: int):
     if name == "lj64k":
         return wl.lj_64k(seed), "mixed", 100, \
             "lj_fluid N=64000 rho=0.84 T=1.2 rc=2.5 shifted rbuff=0.4 dt=0.005"
+    if name == "lj64k_fp64":   # the same fluid on the plain FP64 path
+        return wl.lj_64k(seed), "fp64", 100, \
+            "lj_fluid N=64000 rho=0.84 T=1.2 rc=2.5 shifted rbuff=0.4 dt=0.005 fp64"
     if name == "ka1m":
         return wl.ka_1m(seed), "mixed", 100, \
             "kob_andersen_80_20 N=1000000 rho=1.2 T=1.0 rc=2.5sigma_ij rbuff=0.3 dt=0.005 sort=100"
@@ -491,6 +494,10 @@ def gpu_arm(args):
                      "unit": "GB/s", "frac": round(step_achieved / peak, 4),
                      "alg_bytes_per_step": int(step_bytes), "peak_kind": f"of {peak_kind}"}
 
+    if precision == "fp64":   # the FP64 path is bound by the FP64 pipe, not by memory
+        r_cut = float(np.max(w.pairs.rcut))
+        roofline = dict(fp64_roofline(n, nbar, r["force_ms_mean"], probe_peaks(torch, local),
+                                      r_cut, r_cut + w.r_buff), hbm=roofline)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
            "scaling": "weak",
@@ -813,7 +820,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["gbmd", "reference"], default="gbmd")
-    ap.add_argument("--workload", choices=["lj64k", "ka1m", "plain4k", "paper64k", "paper64k_mixed",
+    ap.add_argument("--workload", choices=["lj64k", "lj64k_fp64", "ka1m", "plain4k", "paper64k",
+                                           "paper64k_mixed",
                                            *POTENTIAL_WORKLOADS, *COLLOID_WORKLOADS,
                                            "batch", "serve"],
                     default="ka1m")
