@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define GBMD_ABI_VERSION 5
+#define GBMD_ABI_VERSION 6
 #define GBMD_MAX_TYPES 4
 
 typedef enum gbmd_status {
@@ -150,6 +150,23 @@ typedef struct gbmd_desc {
                                    for size-disperse systems, where cells sized to the
                                    largest particles hold many small ones).  Uses the
                                    global force path. */
+    int64_t n_ghost;            /* Ghost particles, for a system that is one domain of a
+                                   spatially decomposed one (the paper's MPI domain
+                                   decomposition, Sections 2 and 5): the last n_ghost
+                                   particles in tag order are copies of particles owned by
+                                   other domains (the halo).  They exert forces on the
+                                   others but are not integrated: their positions are
+                                   replaced by gbmd_set_ghost_positions before every step,
+                                   and their own forces, velocities and energies mean
+                                   nothing.  Such a system does not rebuild its lists by
+                                   itself: once one of its own particles has moved more
+                                   than r_buff/2 since the last build, gbmd_get_info
+                                   reports rebuild_pending and the caller rebuilds every
+                                   domain (re-partitioning and recreating them, or
+                                   gbmd_set_state).  0 <= n_ghost < n; ghosts need the NVE
+                                   integrator and the global force path, and a system with
+                                   ghosts cannot join a batch.  Readouts cover every
+                                   particle, ghosts included.  0 = none. */
 } gbmd_desc;
 
 enum { GBMD_PATH_GLOBAL = 0, GBMD_PATH_STAGED = 1 };
@@ -201,6 +218,12 @@ typedef struct gbmd_info {
     double cell_scale;            /* cells are at least cell_scale * r_list,max wide (tree
                                      list: r_list,min; its cells only order the particles) */
     int32_t nlist;                /* GBMD_NLIST_CELL or GBMD_NLIST_TREE */
+    int32_t rebuild_pending;      /* systems with ghosts: one of the system's own
+                                     particles has moved more than r_buff/2 since the last
+                                     build, so every domain must be rebuilt before the
+                                     next step (always 0 without ghosts, which rebuild by
+                                     themselves) */
+    int64_t n_ghost;              /* ghost particles (gbmd_desc.n_ghost) */
 } gbmd_info;
 
 typedef struct gbmd_system gbmd_system;
@@ -285,6 +308,26 @@ int gbmd_get_neighbors(gbmd_system *s, int32_t *counts, int32_t *idx, int64_t ca
 
 /* Configuration and counters. */
 int gbmd_get_info(gbmd_system *s, gbmd_info *out);
+
+/* Domain decomposition (Sections 2 and 5: one system split into spatial domains,
+ * each on its own GPU, exchanging the positions of the particles near their
+ * boundaries every step).  Replace the positions of the system's ghosts (tags
+ * n - n_ghost .. n - 1): pos is n_ghost x 3 in that tag order, any periodic image,
+ * in host memory (device = 0; pageable memory is copied before the call returns,
+ * pinned memory must stay unchanged until the system's stream has reached the
+ * copy) or device memory (device = 1).  Enqueued on the system's stream before the
+ * next step, which then sees the new ghost positions.  BAD_ARG without ghosts or
+ * for NULL pos; STATE while the system is in a batch. */
+int gbmd_set_ghost_positions(gbmd_system *s, const double *pos, int32_t device);
+
+/* Domain decomposition: the wrapped positions ([-L/2, L/2)) of the m particles
+ * whose tags are listed (0 <= tag < n, each at most once or more), written row-major
+ * m x 3 to out, after the system's queued steps.  tags and out are both host
+ * memory (device = 0) or both device memory (device = 1).  Synchronises.  BAD_ARG
+ * for m < 0, m > n, NULL arrays or (host tags) a tag out of range; a device tag
+ * out of range gives NaN in its row. */
+int gbmd_get_positions(gbmd_system *s, const int32_t *tags, int64_t m, double *out,
+                       int32_t device);
 
 /* Device bytes a system with this description would hold (for admission
  * control); returns a negative gbmd_status for an invalid description. */

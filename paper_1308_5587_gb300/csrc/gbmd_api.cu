@@ -590,6 +590,9 @@ int validate(const gbmd_desc* d, bool device) {
   if (d->integrator == GBMD_NVT &&
       (!(d->kT > 0) || !(d->tau > 0) || !std::isfinite(d->kT) || !std::isfinite(d->tau) || d->n < 2))
     return fail(GBMD_ERR_BAD_ARG, "NVT needs kT > 0, tau > 0 and at least 2 particles");
+  if (d->n_ghost < 0 || d->n_ghost >= d->n) return fail(GBMD_ERR_BAD_ARG, "n_ghost must be in [0, n)");
+  if (d->n_ghost > 0 && (d->integrator != GBMD_NVE || d->force_path != GBMD_PATH_GLOBAL))
+    return fail(GBMD_ERR_BAD_ARG, "ghosts need the NVE integrator and the global force path");
   const int nt = d->ntypes;
   double rmax = 0;
   RET(validate_pairs(d, &rmax));
@@ -853,6 +856,7 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   SysDev& h = s->h;
   const int n = (int)d->n, nt = d->ntypes;
   h.n = n;
+  h.n_ghost = (int)d->n_ghost;
   h.ntypes = nt;
   h.precision = d->precision;
   h.sort_period = d->sort_period;
@@ -1536,6 +1540,54 @@ int gbmd_get_info(gbmd_system* s, gbmd_info* out) {
   out->max_window = f.max_window;
   out->cell_scale = s->cell_scale;
   out->nlist = s->h.tree ? GBMD_NLIST_TREE : GBMD_NLIST_CELL;
+  out->rebuild_pending = s->h.n_ghost > 0 && f.rebuild_req ? 1 : 0;
+  out->n_ghost = s->h.n_ghost;
+  return GBMD_OK;
+}
+
+int gbmd_set_ghost_positions(gbmd_system* s, const double* pos, int32_t device) {
+  if (!s || !pos) return fail(GBMD_ERR_BAD_ARG, "NULL argument");
+  if (s->h.n_ghost <= 0) return fail(GBMD_ERR_BAD_ARG, "the system has no ghosts");
+  if (s->batch) return fail(GBMD_ERR_STATE, "the system is in a batch");
+  RET(use_device(s->device));
+  Group* g = s->own;
+  RET(sync_layout(g));
+  cudaStream_t st = cur_stream(s);
+  const double* dp = pos;
+  if (!device) {   // staging: the import buffer holds n >= n_ghost rows
+    CK(cudaMemcpyAsync(s->d_pos, pos, (size_t)s->h.n_ghost * 24, cudaMemcpyHostToDevice, st));
+    dp = s->d_pos;
+  }
+  CK(launch(ghost_set_call(g->d_desc, s->h.n_ghost, dp), st));
+  return GBMD_OK;
+}
+
+int gbmd_get_positions(gbmd_system* s, const int32_t* tags, int64_t m, double* out,
+                       int32_t device) {
+  if (!s || !tags || !out) return fail(GBMD_ERR_BAD_ARG, "NULL argument");
+  if (m < 0 || m > s->h.n) return fail(GBMD_ERR_BAD_ARG, "m must be in [0, n]");
+  if (!device)
+    for (int64_t k = 0; k < m; ++k)
+      if (tags[k] < 0 || tags[k] >= s->h.n) return fail(GBMD_ERR_BAD_ARG, "tag %d out of range", tags[k]);
+  RET(use_device(s->device));
+  RET(sync_system(s));
+  if (m == 0) return GBMD_OK;
+  Group* g = s->batch ? s->batch : s->own;
+  RET(sync_layout(g));
+  int idx = 0;   // the system's slot in its group's descriptor array
+  for (size_t k = 0; k < g->members.size(); ++k)
+    if (g->members[k] == s) idx = (int)k;
+  cudaStream_t st = cur_stream(s);
+  const int* dt = tags;
+  double* dout = out;
+  if (!device) {   // staging: the import buffers hold n >= m rows
+    CK(cudaMemcpyAsync(s->d_type, tags, (size_t)m * 4, cudaMemcpyHostToDevice, st));
+    dt = s->d_type;
+    dout = s->d_pos;
+  }
+  CK(launch(gather_pos_call(g->d_desc + idx, dt, (int)m, dout), st));
+  if (!device) CK(cudaMemcpyAsync(out, s->d_pos, (size_t)m * 24, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return GBMD_OK;
 }
 
@@ -1639,6 +1691,7 @@ int gbmd_batch_add(gbmd_batch* bh, gbmd_system* s, int32_t* slot) {
   if (!b || !s || !slot) return fail(GBMD_ERR_BAD_ARG, "NULL argument");
   RET(use_device(reinterpret_cast<Group*>(bh)->device));
   if (s->batch) return fail(GBMD_ERR_STATE, "system already in a batch");
+  if (s->h.n_ghost > 0) return fail(GBMD_ERR_BAD_ARG, "a system with ghosts cannot join a batch");
   if (s->h.precision != b->precision) return fail(GBMD_ERR_BAD_ARG, "precision mismatch");
   for (auto* m : live(b)) {
     if (m->h.nvt != s->h.nvt) return fail(GBMD_ERR_BAD_ARG, "a batch holds NVE or NVT systems, not both");

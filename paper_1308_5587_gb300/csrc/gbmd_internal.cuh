@@ -131,6 +131,10 @@ struct SysDev {
   // type tree_qtype[k]
   int tree_qpos[MAXT + 1], tree_qtype[MAXT];
   int n, ntypes, cap, precision;
+  // domain decomposition: the last n_ghost tags are ghosts (not integrated; their
+  // positions are set from outside every step); such a system leaves its rebuilds to
+  // the caller (the step records rebuild_req and does not act on it)
+  int n_ghost;
   int nl_stride;           // particles per slot group of the list (N rounded up to 32)
   // staged force path (mixed precision, >= 4 cells per axis): the list holds 16-bit
   // window-local indices in ELL8 layout, indexed by member rank (cell order)

@@ -197,6 +197,56 @@ __global__ void __launch_bounds__(TILE_P) k_nlist_export(const SysDev* __restric
 }
 
 // ---------------------------------------------------------------------------
+// domain decomposition: ghost positions in, selected positions out
+// ---------------------------------------------------------------------------
+// ghost k (tag n - n_ghost + k) takes pos[k] (row-major, real units, any image):
+// x, the current step's shadow and, in FP64, its gather copy; the image counts of a
+// ghost are not kept
+__global__ void __launch_bounds__(TILE_P) k_ghost_set(const SysDev* __restrict__ d,
+                                                      const double* __restrict__ pos) {
+  const SysDev& s = *d;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= s.n_ghost) return;
+  const int n = s.n;
+  const int i = s.rtag[n - s.n_ghost + k];
+  const long long step = step_of(s.flags);
+  int q[3];
+  double xr[3];
+  for (int a = 0; a < 3; ++a) {
+    const double L = s.L[a];
+    double x = pos[3 * (size_t)k + a];
+    x -= floor((x + 0.5 * L) / L) * L;   // centred box [-L/2, L/2)
+    if (x >= 0.5 * L) x -= L;
+    if (x < -0.5 * L) x += L;
+    double xq = x * s.qscale[a];
+    long long qq = __double2ll_rn(xq);
+    if (qq >= 0x80000000LL) { xq -= 4294967296.0; qq -= 0x100000000LL; }
+    s.x[a * n + i] = xq;
+    q[a] = (int)qq;
+    xr[a] = xq * (L / 4294967296.0);
+  }
+  const int ty = s.type[i];
+  q_at(s, step)[i] = make_int4(q[0], q[1], q[2], ty);
+  if (s.precision == GBMD_FP64)
+    p64_at(s, step)[i] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
+}
+
+// out[k] = the wrapped position of the particle with tag tags[k] (NaN for a tag out
+// of range)
+__global__ void __launch_bounds__(TILE_P) k_gather_pos(const SysDev* __restrict__ d,
+                                                       const int* __restrict__ tags, int m,
+                                                       double* __restrict__ out) {
+  const SysDev& s = *d;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const int tg = tags[k], n = s.n;
+  const bool ok = tg >= 0 && tg < n;
+  const int i = ok ? s.rtag[tg] : 0;
+  for (int a = 0; a < 3; ++a)
+    out[3 * (size_t)k + a] = ok ? s.x[a * n + i] * (s.L[a] / 4294967296.0) : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// ---------------------------------------------------------------------------
 // launch plumbing
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -247,6 +297,18 @@ KernelCall nlist_export_call(const SysDev* d, const Tile* tiles_p, int ntiles, i
                              int* idx, int cap_out, int* too_many) {
   KernelCall k = mk((void*)k_nlist_export, ntiles, TILE_P);
   put(k, d); put(k, tiles_p); put(k, counts); put(k, idx); put(k, cap_out); put(k, too_many);
+  return k;
+}
+
+KernelCall ghost_set_call(const SysDev* d, int n_ghost, const double* pos) {
+  KernelCall k = mk((void*)k_ghost_set, (n_ghost + TILE_P - 1) / TILE_P, TILE_P);
+  put(k, d); put(k, pos);
+  return k;
+}
+
+KernelCall gather_pos_call(const SysDev* d, const int* tags, int m, double* out) {
+  KernelCall k = mk((void*)k_gather_pos, (m + TILE_P - 1) / TILE_P, TILE_P);
+  put(k, d); put(k, tags); put(k, m); put(k, out);
   return k;
 }
 

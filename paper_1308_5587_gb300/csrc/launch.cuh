@@ -77,6 +77,11 @@ KernelCall import_call(const SysDev* d, const Tile* tiles_p, int ntiles, const d
                        const double* vel, const int* type, const int* image);
 KernelCall export_call(const SysDev* d, const Tile* tiles_p, int ntiles, double* pos,
                        double* vel, int* image, double* force, double* pp_u, double* pp_w);
+// domain decomposition (one system, d pointing at its descriptor): ghost positions
+// (row-major, real units) into the current step's state; wrapped positions of listed
+// tags out
+KernelCall ghost_set_call(const SysDev* d, int n_ghost, const double* pos);
+KernelCall gather_pos_call(const SysDev* d, const int* tags, int m, double* out);
 // neighbour rows -> tag-order rows sorted ascending (test readout)
 KernelCall nlist_export_call(const SysDev* d, const Tile* tiles_p, int ntiles, int* counts,
                              int* idx, int cap_out, int* too_many);

@@ -79,6 +79,20 @@ __device__ __forceinline__ void integrate_one(const SysDev& s, int i, int ty, co
                                               double4_32a* __restrict__ p64_next, bool& need,
                                               bool& bad) {
   const int n = s.n;
+  if (s.n_ghost > 0 && __ldg(s.tag + i) >= n - s.n_ghost) {
+    // a ghost (a copy of a particle another domain owns) keeps the position set
+    // before the step: no kick, drift or displacement check; the next shadow repeats
+    // the current one
+    const int4 qg = make_int4((int)rint_ll(p0.xq[0]), (int)rint_ll(p0.xq[1]),
+                              (int)rint_ll(p0.xq[2]), ty);
+    q_next[i] = qg;
+    if (PREC == GBMD_FP64)
+      p64_next[i] = make_double4_32a(p0.xq[0] * (s.L[0] * (1.0 / 4294967296.0)),
+                                     p0.xq[1] * (s.L[1] * (1.0 / 4294967296.0)),
+                                     p0.xq[2] * (s.L[2] * (1.0 / 4294967296.0)),
+                                     __longlong_as_double(ty));
+    return;
+  }
   const double kick = vfull ? s.h : s.h + s.h;
   double v[3], xq[3];
   int q[3];
@@ -226,13 +240,16 @@ __device__ __forceinline__ void step_tail(const SysDev& s, const SysDev* __restr
     const long long nsort = g->n_sorts;
     const int sp = sysv[k].sort_period;
     const bool act = w.error == 0 && (sl.y < 0 || sl.x < sl.y);
+    // a domain with ghosts only records the request: its caller rebuilds every domain
+    const bool ext = sysv[k].n_ghost > 0;
     if (act) {
       const long long st = sl.x + 1;
-      const int rb = w.rebuild_req;
+      const int req = w.rebuild_req;
+      const int rb = ext ? 0 : req;
       const int srt = rb && sp > 0 && (st - lr.x >= sp);
       g->step = st;
       g->v_full = 0;
-      g->rebuild_req = 0;
+      g->rebuild_req = ext ? req : 0;
       g->do_rebuild = rb;
       if (rb) g->n_rebuilds = lr.y + 1;
       if (srt) {

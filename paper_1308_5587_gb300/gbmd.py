@@ -43,7 +43,7 @@ class gbmd_desc(C.Structure):
                 ("stream", C.c_void_p), ("device", C.c_int32), ("force_path", C.c_int32),
                 ("integrator", C.c_int32), ("kT", C.c_double), ("tau", C.c_double),
                 ("potential", C.c_int32), ("mie_n", C.c_void_p), ("mie_m", C.c_void_p),
-                ("kappa", C.c_void_p), ("nlist", C.c_int32)]
+                ("kappa", C.c_void_p), ("nlist", C.c_int32), ("n_ghost", C.c_int64)]
 
 
 GBMD_PATH_GLOBAL, GBMD_PATH_STAGED = 0, 1
@@ -77,7 +77,8 @@ class gbmd_info(C.Structure):
                 ("step", C.c_int64), ("n_rebuilds", C.c_int64), ("n_sorts", C.c_int64),
                 ("kernel_launches", C.c_int64), ("neighbors_total", C.c_int64),
                 ("footprint_bytes", C.c_int64), ("force_path", C.c_int32),
-                ("max_window", C.c_int32), ("cell_scale", C.c_double), ("nlist", C.c_int32)]
+                ("max_window", C.c_int32), ("cell_scale", C.c_double), ("nlist", C.c_int32),
+                ("rebuild_pending", C.c_int32), ("n_ghost", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -122,6 +123,8 @@ _SIGS = {
     "gbmd_abi_version": (C.c_int, []),
     "gbmd_probe_arith": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double),
                                    C.POINTER(C.c_float)]),
+    "gbmd_set_ghost_positions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "gbmd_get_positions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32]),
 }
 
 
@@ -169,7 +172,8 @@ def _stream_handle(stream):
 def make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass, precision,
               sort_period=0, nlist_capacity=0, threads_per_particle=0, stream=None,
               image=None, device=False, cuda_device=-1, force_path="global", integrator="nve",
-              kT=0.0, tau=0.0, potential="lj", mie_n=None, mie_m=None, kappa=None, nlist="cell"):
+              kT=0.0, tau=0.0, potential="lj", mie_n=None, mie_m=None, kappa=None, nlist="cell",
+              n_ghost=0):
     """Build a gbmd_desc; returns (desc, keepalive) -- keep the second alive.  Pair
     tables are ntypes x ntypes arrays or scalars; a table the potential does not read
     may be None (sigma for Yukawa, rcut for WCA, mie_n / mie_m / kappa elsewhere)."""
@@ -215,6 +219,7 @@ def make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass, preci
     d.potential = POTENTIALS.get(potential, potential) if isinstance(potential, str) else int(potential)
     d.mie_n, d.mie_m, d.kappa = _ptr(mie_n), _ptr(mie_m), _ptr(kappa)
     d.nlist = NLISTS.get(nlist, nlist) if isinstance(nlist, str) else int(nlist)
+    d.n_ghost = int(n_ghost)
     return d, keep
 
 
@@ -297,6 +302,29 @@ def gbmd_get_info(h) -> dict:
     i = gbmd_info()
     _check(load().gbmd_get_info(h, C.byref(i)))
     return i.as_dict()
+
+
+def gbmd_set_ghost_positions(h, pos, device: bool = False):
+    """Ghost positions (n_ghost x 3, ghost tag order): a host array, or a device
+    pointer (int) with device=True."""
+    if device:
+        _check(load().gbmd_set_ghost_positions(h, int(pos), 1))
+        return
+    p = np.ascontiguousarray(pos, np.float64)
+    _check(load().gbmd_set_ghost_positions(h, _ptr(p), 0))
+
+
+def gbmd_get_positions(h, tags, out=None):
+    """Wrapped positions (m x 3) of the particles with the given tags (host arrays)."""
+    t = np.ascontiguousarray(tags, np.int32).ravel()
+    out = np.empty((t.size, 3), np.float64) if out is None else out
+    _check(load().gbmd_get_positions(h, _ptr(t), t.size, _ptr(out), 0))
+    return out
+
+
+def gbmd_get_positions_device(h, tags_ptr: int, m: int, out_ptr: int):
+    """As gbmd_get_positions with device pointers (int32 tags, m x 3 FP64 out)."""
+    _check(load().gbmd_get_positions(h, int(tags_ptr), int(m), int(out_ptr), 1))
 
 
 def gbmd_footprint_bytes(desc: gbmd_desc) -> int:
@@ -408,12 +436,12 @@ class System:
                  dt=0.005, mass=1.0, precision="mixed", sort_period=0, nlist_capacity=0,
                  threads_per_particle=0, stream=None, image=None, device=False, n=None,
                  cuda_device=-1, force_path="global", integrator="nve", kT=0.0, tau=0.0,
-                 potential="lj", mie_n=None, mie_m=None, kappa=None, nlist="cell"):
+                 potential="lj", mie_n=None, mie_m=None, kappa=None, nlist="cell", n_ghost=0):
         n = int(n if n is not None else np.asarray(pos).reshape(-1, 3).shape[0])
         desc, keep = make_desc(n, box, pos, vel, types, eps, sigma, rcut, r_buff, dt, mass,
                                precision, sort_period, nlist_capacity, threads_per_particle,
                                stream, image, device, cuda_device, force_path, integrator, kT, tau,
-                               potential, mie_n, mie_m, kappa, nlist)
+                               potential, mie_n, mie_m, kappa, nlist, n_ghost)
         self.n = n
         self.box = np.broadcast_to(np.asarray(box, np.float64), (3,)).copy()
         self.precision = precision
@@ -466,6 +494,12 @@ class System:
 
     def set_cell_scale(self, scale: float):
         gbmd_set_cell_scale(self.handle, scale)
+
+    def set_ghost_positions(self, pos):
+        gbmd_set_ghost_positions(self.handle, pos)
+
+    def positions(self, tags, out=None):
+        return gbmd_get_positions(self.handle, tags, out)
 
     def set_thermostat(self, xi: float, eta: float):
         gbmd_set_thermostat(self.handle, xi, eta)

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.gbmd_abi_version() == 5
+    assert lib.gbmd_abi_version() == 6
 
 
 def _desc(lib, **over):
@@ -138,3 +138,24 @@ def test_probe_rejects_bad_arguments_before_any_launch(lib):
         with pytest.raises(lib.GbmdError) as e:
             lib.gbmd_probe_arith(kind, iters)
         assert e.value.status == "BAD_ARG"
+
+
+@pytest.mark.parametrize("over,msg", [
+    (dict(n_ghost=-1), "n_ghost"),
+    (dict(n_ghost=4), "n_ghost"),
+    (dict(n_ghost=1, integrator="nvt", kT=1.0, tau=1.0), "ghosts need"),
+    (dict(n_ghost=1, force_path="staged"), "ghosts need"),
+])
+def test_ghost_arguments_are_checked_on_the_host(lib, over, msg):
+    d, keep = _desc(lib, **over)
+    with pytest.raises(lib.GbmdError) as e:
+        lib.gbmd_create(d)
+    assert e.value.status == "BAD_ARG" and msg in str(e.value)
+
+
+def test_ghost_calls_reject_null_arguments(lib):
+    with pytest.raises(lib.GbmdError):
+        lib.gbmd_set_ghost_positions(None, np.zeros((1, 3)))
+    import ctypes
+    so = lib.load()
+    assert so.gbmd_get_positions(None, None, 0, None, 0) == -1
