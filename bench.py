@@ -380,9 +380,15 @@ def run_system(torch, w, precision, sort_period, stream, dist, local, flush, ste
     t_local = float(step_ms.sum()) / 1e3
     t_max = reduce_scalar(dist, t_local, "max")
     units = reduce_scalar(dist, w.n * steps, "sum")
+    # steps that rebuilt the lists stand out: well above the median step
+    med = float(np.median(step_ms))
+    reb = step_ms[step_ms > 1.8 * med]
+    split = {"median_step_ms": round(med, 5),
+             "rebuild_steps": int(reb.size),
+             "rebuild_step_ms_mean": round(float(reb.mean()), 5) if reb.size else None}
     return {"value": units / t_max, "t_max": t_max, "ms_per_step": 1e3 * t_max / steps,
             "step_ms_mean": float(step_ms.mean()), "force_ms_mean": float(force_ms.mean()),
-            "launches": int(launches), "info": info, "clocks": clk}
+            "launches": int(launches), "info": info, "clocks": clk, "split": split}
 
 
 def hbm_roofline(n, nbar, precision, force_ms, step_ms, info, workload):
@@ -516,6 +522,7 @@ def gpu_arm(args):
                       "force_path": "staged" if info["force_path"] == 1 else "global",
                       "sort_period": sort_period},
            "tps": args.steps / r["t_max"], "roofline": roofline, "roofline_step": roofline_step,
+           "step_split": r["split"],
            "clocks": r["clocks"], "gpu_launches": r["launches"],
            "rebuilds_per_step": round(reb, 4)}
 
