@@ -9,10 +9,12 @@ one velocity-Verlet time step of the whole path: the step kernel (pair force, th
 kick, drift, wrap, shadow and the rebuild check) and the conditional
 cell-list/neighbour-list rebuild that follows it.
 
-Timing: W untimed warm-up steps, then exactly K steps, each bracketed by CUDA
-events on the system's stream.  At 10^6 particles the inputs (the neighbour list
-alone is ~370 MB) exceed the 129 MB L2; smaller workloads write 256 MB between steps
-so that every step starts with a cold L2.  A second, shorter pass brackets the
+Timing: W untimed warm-up steps, then exactly K steps between CUDA events on the
+system's stream.  At 10^6 particles the inputs (the neighbour list alone is ~370 MB)
+exceed the 129 MB L2, and the K steps are one gbmd_step(K) call (run as 16-step CUDA
+graphs) between one pair of events; smaller workloads write 256 MB between steps so
+that every step starts with a cold L2, and each step is then bracketed by its own
+pair of events.  A second, shorter pass brackets the
 force kernel of every step with its own pair of events (event nodes inside the
 step graph) for the roofline figure; those nodes add a few microseconds to a step,
 so the headline pass runs without them.  Clocks are sampled with nvidia-smi during
@@ -235,12 +237,15 @@ def recorded_traffic(workload: str, precision: str):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def timed_steps(torch, s, K: int, W: int, flush, stream, dist, force_events: bool = False):
+def timed_steps(torch, s, K: int, W: int, flush, stream, dist, force_events: bool = False,
+                region: bool = False):
     """W warm-up steps, then K steps each bracketed by events on the stream; returns
     per-step milliseconds, per-force-kernel milliseconds (force_events: event nodes
     around the force kernel inside the step graph, which add a few microseconds to
     the step, so the headline pass runs without them) and the number of library
-    kernels executed."""
+    kernels executed.  region (inputs larger than L2, nothing between steps): the K
+    steps are one call, run as the library runs them (16-step CUDA graphs), between
+    one pair of events; every step is then given the mean."""
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     for e4 in ev:                    # torch creates the CUDA events at the first record
         for e in e4:
@@ -256,19 +261,28 @@ def timed_steps(torch, s, K: int, W: int, flush, stream, dist, force_events: boo
     barrier(dist)
     torch.cuda.synchronize()
     l0 = s.info()["kernel_launches"]
-    for k in range(K):
-        if flush is not None:
-            flush.zero_()
-        if force_events:
-            s.set_force_events(ev[k][1], ev[k][2])
-        ev[k][0].record(stream)
-        s.step(1)
-        ev[k][3].record(stream)
+    whole = region and flush is None and not force_events
+    if whole:
+        ev[0][0].record(stream)
+        s.step(K)
+        ev[0][3].record(stream)
+    else:
+        for k in range(K):
+            if flush is not None:
+                flush.zero_()
+            if force_events:
+                s.set_force_events(ev[k][1], ev[k][2])
+            ev[k][0].record(stream)
+            s.step(1)
+            ev[k][3].record(stream)
     torch.cuda.synchronize()
     barrier(dist)
     s.sync()
     l1 = s.info()["kernel_launches"]
-    step_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
+    if whole:
+        step_ms = np.full(K, ev[0][0].elapsed_time(ev[0][3]) / K)
+    else:
+        step_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
     force_ms = None
     if force_events:
         s.set_force_events(None, None)
@@ -369,10 +383,11 @@ def run_system(torch, w, precision, sort_period, stream, dist, local, flush, ste
     clocks = ClockSampler(local) if sample_clocks else None
     if clocks:
         clocks.start()
-    step_ms, _, launches = timed_steps(torch, s, steps, warmup, flush, stream, dist)
+    step_ms, _, launches = timed_steps(torch, s, steps, warmup, flush, stream, dist,
+                                       region=True)
     clk = clocks.stop() if clocks else None
-    _, force_ms, _ = timed_steps(torch, s, min(steps, 1000), 3, flush, stream, dist,
-                                 force_events=True)
+    step1_ms, force_ms, _ = timed_steps(torch, s, min(steps, 1000), 3, flush, stream, dist,
+                                        force_events=True)
     info = s.info()
     th = s.thermo()
     s.close()
@@ -380,12 +395,14 @@ def run_system(torch, w, precision, sort_period, stream, dist, local, flush, ste
     t_local = float(step_ms.sum()) / 1e3
     t_max = reduce_scalar(dist, t_local, "max")
     units = reduce_scalar(dist, w.n * steps, "sum")
-    # steps that rebuilt the lists stand out: well above the median step
-    med = float(np.median(step_ms))
-    reb = step_ms[step_ms > 1.8 * med]
+    # steps that rebuilt the lists stand out: well above the median step (second pass,
+    # single-step graphs with the force-kernel event nodes)
+    med = float(np.median(step1_ms))
+    reb = step1_ms[step1_ms > 1.8 * med]
     split = {"median_step_ms": round(med, 5),
-             "rebuild_steps": int(reb.size),
-             "rebuild_step_ms_mean": round(float(reb.mean()), 5) if reb.size else None}
+             "rebuild_steps": int(reb.size), "of_steps": int(step1_ms.size),
+             "rebuild_step_ms_mean": round(float(reb.mean()), 5) if reb.size else None,
+             "pass": "single-step graphs with event nodes around the force kernel"}
     return {"value": units / t_max, "t_max": t_max, "ms_per_step": 1e3 * t_max / steps,
             "step_ms_mean": float(step_ms.mean()), "force_ms_mean": float(force_ms.mean()),
             "launches": int(launches), "info": info, "clocks": clk, "split": split}
@@ -514,9 +531,12 @@ def gpu_arm(args):
                       "parallelism": f"replicas x{world}" if world > 1 else "single system",
                       "l2": "flushed between steps (256 MB write)" if flush is not None
                       else "inputs larger than L2 (nlist > 129 MB)",
-                      "timed_iteration": "one MD step (" + ("direct kernel launches" if
-                                                            args.no_graphs else
-                                                            "one single-step CUDA graph") + ")",
+                      "timed_iteration": ("one MD step per event pair (direct kernel launches)"
+                                          if args.no_graphs else
+                                          "one MD step per event pair (single-step CUDA graph)"
+                                          if flush is not None else
+                                          "all K steps between one event pair, as one "
+                                          "gbmd_step(K) call (16-step CUDA graphs)"),
                       "threads_per_particle": info["threads_per_particle"],
                       "force_block": info["force_block"], "nlist_capacity": info["nlist_capacity"],
                       "force_path": "staged" if info["force_path"] == 1 else "global",
@@ -627,7 +647,8 @@ def run_batch(torch, replicas, steps, warmup, stream, dist, local, autotune=True
     clocks = ClockSampler(local)
     clocks.start()
     stepper = _BatchStepper(b, systems)
-    step_ms, _, launches = timed_steps(torch, stepper, steps, warmup, None, stream, dist)
+    step_ms, _, launches = timed_steps(torch, stepper, steps, warmup, None, stream, dist,
+                                       region=True)
     clk = clocks.stop()
     _, force_ms, _ = timed_steps(torch, stepper, min(steps, 500), 3, None, stream, dist,
                                  force_events=True)
@@ -652,7 +673,8 @@ def run_batch(torch, replicas, steps, warmup, stream, dist, local, autotune=True
             "n": n, "replicas": len(ws), "threads_per_particle": tune[0],
             "force_block": tune[1], "autotuned": bool(autotune),
             "l2": "inputs larger than L2",
-            "timed_iteration": "one step of every replica (one single-step CUDA graph)",
+            "timed_iteration": "all K steps of every replica between one event pair, as one "
+                               "gbmd_batch_step(K) call (16-step CUDA graphs)",
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                          "kernel": "k_force<mixed> (step mode) over all replicas",

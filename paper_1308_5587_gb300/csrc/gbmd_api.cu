@@ -18,6 +18,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.cuh"
 
 using namespace gbmd;
@@ -55,6 +57,13 @@ constexpr int STEPS_PER_GRAPH = 16;
 constexpr int STAGED_WINDOW_CAP = 3072;   // window particles in 48 KB of shared memory
 
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+// NVTX range over a host call (the timeline of a profiler shows the library's
+// calls: enqueues, rebuild recoveries, readouts); a no-op unless a tool is attached
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 }  // namespace
 
@@ -430,8 +439,12 @@ int enqueue_steps(Group* g, long long n) {
   for (long long k = 0; k < n; ++k) {
     const bool events = n == 1 && g->ev_begin && g->ev_end;
     if (events) CK(cudaEventRecord(g->ev_begin, g->stream));
-    for (const KernelCall& c : step_calls(g, 0, 0)) CK(launch(c, g->stream));
+    {
+      Range r("gbmd step kernel launches");
+      for (const KernelCall& c : step_calls(g, 0, 0)) CK(launch(c, g->stream));
+    }
     if (events) CK(cudaEventRecord(g->ev_end, g->stream));
+    Range r("gbmd rebuild kernel launches");
     for (const KernelCall& c : rebuild_calls(g)) CK(launch(c, g->stream));
   }
   return GBMD_OK;
@@ -504,6 +517,7 @@ int sync_system(gbmd_system* s) {
       continue;
     }
     if (f.error == DEV_OVERFLOW) {
+      Range r("gbmd neighbour-list overflow recovery");
       RET(grow_nlist(s, std::max(f.overflow_need, s->h.cap + 1)));
       f.error = 0;
       f.overflow_need = 0;
@@ -1347,6 +1361,7 @@ int gbmd_probe_arith(int32_t kind, int32_t iters, void* stream, double* ops, flo
 }
 
 int gbmd_create(const gbmd_desc* d, gbmd_system** out) {
+  Range nvtx_range("gbmd_create");
   RET(create_impl(d, out, false));
   int rc = load_state(*out, d->pos, d->vel, d->type, d->image, false, 0);
   if (rc != GBMD_OK) {
@@ -1359,6 +1374,7 @@ int gbmd_create(const gbmd_desc* d, gbmd_system** out) {
 }
 
 int gbmd_create_device(const gbmd_desc* d, gbmd_system** out) {
+  Range nvtx_range("gbmd_create_device");
   RET(create_impl(d, out, true));
   int rc = load_state(*out, d->pos, d->vel, d->type, d->image, true, 0);
   if (rc != GBMD_OK) {
@@ -1395,6 +1411,7 @@ int gbmd_destroy(gbmd_system* s) {
 }
 
 int gbmd_step(gbmd_system* s, int64_t nsteps) {
+  Range nvtx_range("gbmd_step");
   if (!s || nsteps < 0) return fail(GBMD_ERR_BAD_ARG, "bad system or nsteps");
   RET(use_device(s->device));
   if (s->batch) return fail(GBMD_ERR_STATE, "system belongs to a batch; use gbmd_batch_step");
@@ -1403,12 +1420,14 @@ int gbmd_step(gbmd_system* s, int64_t nsteps) {
 }
 
 int gbmd_sync(gbmd_system* s) {
+  Range nvtx_range("gbmd_sync");
   if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
   RET(use_device(s->device));
   return sync_system(s);
 }
 
 int gbmd_get_forces(gbmd_system* s, double* out) {
+  Range nvtx_range("gbmd_get_forces");
   if (!s || !out) return fail(GBMD_ERR_BAD_ARG, "NULL argument");
   RET(use_device(s->device));
   RET(sync_system(s));
@@ -1416,6 +1435,7 @@ int gbmd_get_forces(gbmd_system* s, double* out) {
 }
 
 int gbmd_get_thermo(gbmd_system* s, gbmd_thermo* out) {
+  Range nvtx_range("gbmd_get_thermo");
   if (!s || !out) return fail(GBMD_ERR_BAD_ARG, "NULL argument");
   RET(use_device(s->device));
   RET(sync_system(s));
@@ -1437,6 +1457,7 @@ int gbmd_get_thermo(gbmd_system* s, gbmd_thermo* out) {
 }
 
 int gbmd_get_per_particle(gbmd_system* s, double* energy, double* virial) {
+  Range nvtx_range("gbmd_get_per_particle");
   if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
   RET(use_device(s->device));
   RET(sync_system(s));
@@ -1454,6 +1475,7 @@ int gbmd_get_per_particle(gbmd_system* s, double* energy, double* virial) {
 }
 
 int gbmd_get_state(gbmd_system* s, double* pos, double* vel, int32_t* image, int64_t* step) {
+  Range nvtx_range("gbmd_get_state");
   if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
   RET(use_device(s->device));
   RET(sync_system(s));
@@ -1468,6 +1490,7 @@ int gbmd_get_state(gbmd_system* s, double* pos, double* vel, int32_t* image, int
 
 int gbmd_set_state(gbmd_system* s, const double* pos, const double* vel, const int32_t* image,
                    int64_t step) {
+  Range nvtx_range("gbmd_set_state");
   if (!s || !pos || !vel || step < 0) return fail(GBMD_ERR_BAD_ARG, "bad argument");
   RET(use_device(s->device));
   if (s->batch) return fail(GBMD_ERR_STATE, "remove the system from its batch first");
@@ -1487,6 +1510,7 @@ int gbmd_set_state(gbmd_system* s, const double* pos, const double* vel, const i
 }
 
 int gbmd_get_neighbors(gbmd_system* s, int32_t* counts, int32_t* idx, int64_t cap) {
+  Range nvtx_range("gbmd_get_neighbors");
   if (!s || !counts || !idx || cap < 1 || cap > (1 << 20)) return fail(GBMD_ERR_BAD_ARG, "bad argument");
   RET(use_device(s->device));
   RET(sync_system(s));
@@ -1655,6 +1679,7 @@ int gbmd_set_force_events(gbmd_system* s, void* ev_begin, void* ev_end) {
 }
 
 int gbmd_autotune(gbmd_system* s, const char* cache_path) {
+  Range nvtx_range("gbmd_autotune");
   if (!s) return fail(GBMD_ERR_BAD_ARG, "system is NULL");
   RET(use_device(s->device));
   if (s->batch) return fail(GBMD_ERR_STATE, "system belongs to a batch");
@@ -1734,6 +1759,7 @@ int gbmd_batch_remove(gbmd_batch* bh, int32_t slot) {
 }
 
 int gbmd_batch_step(gbmd_batch* bh, int64_t nsteps) {
+  Range nvtx_range("gbmd_batch_step");
   Group* b = reinterpret_cast<Group*>(bh);
   if (!b || nsteps < 0) return fail(GBMD_ERR_BAD_ARG, "bad argument");
   RET(use_device(reinterpret_cast<Group*>(bh)->device));
@@ -1742,6 +1768,7 @@ int gbmd_batch_step(gbmd_batch* bh, int64_t nsteps) {
 }
 
 int gbmd_batch_sync(gbmd_batch* bh) {
+  Range nvtx_range("gbmd_batch_sync");
   Group* b = reinterpret_cast<Group*>(bh);
   if (!b) return fail(GBMD_ERR_BAD_ARG, "NULL batch");
   RET(use_device(reinterpret_cast<Group*>(bh)->device));
@@ -1760,6 +1787,7 @@ int gbmd_batch_sync(gbmd_batch* bh) {
 }
 
 int gbmd_batch_autotune(gbmd_batch* bh, const char* cache_path) {
+  Range nvtx_range("gbmd_batch_autotune");
   Group* b = reinterpret_cast<Group*>(bh);
   if (!b) return fail(GBMD_ERR_BAD_ARG, "NULL batch");
   RET(use_device(reinterpret_cast<Group*>(bh)->device));

@@ -17,6 +17,8 @@
 //     band of 1e-5 of r_list^2 are decided again in FP64 with the same operations
 //     (and rounding) as the brute-force reference definition, and appended after
 //     the other hits of their chunk of 32 candidates.
+#include <algorithm>
+
 #include "launch.cuh"
 #include "nlist_core.cuh"
 
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(TILE_P) k_bin(const SysDev* __restrict__ sysv,
   const Tile t = tiles[blockIdx.x];
   const SysDev& s = sysv[t.sys];
   count(s, t, ctl);
-  if (!rebuilding(s) || threadIdx.x >= t.count) return;
+  if (!block_rebuilding(s) || threadIdx.x >= t.count) return;
   const int i = t.first + threadIdx.x;
   const int4 q = q_at(s, step_of(s.flags))[i];
   const int cx = cell_of_fixed(q.x, s.nc[0]);
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(TILE_P) k_scatter(const SysDev* __restrict__ s
   const Tile t = tiles[blockIdx.x];
   const SysDev& s = sysv[t.sys];
   count(s, t, ctl);
-  if (!rebuilding(s) || threadIdx.x >= t.count) return;
+  if (!block_rebuilding(s) || threadIdx.x >= t.count) return;
   const int i = t.first + threadIdx.x;
   const int p = atomicAdd(&s.cell_cursor[s.key[i]], 1);
   s.members_tmp[p] = i;
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* 
   const SysDev& s = sysv[t.sys];
   count(s, t, ctl);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (!rebuilding(s) || w >= t.count) return;
+  if (!block_rebuilding(s) || w >= t.count) return;
   const int r = t.first + w;
   const int b = s.cell_start[r], e = s.cell_start[r + 1], n = e - b;
   const bool fine = s.tree != 0;
@@ -174,52 +176,76 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* 
 }
 
 // ---- re-sort: gather every per-particle array into cell order ----
+// Both kernels run at every rebuild and do work only when the system re-sorts, so
+// they walk the tile table with a grid of at most RESORT_BLOCKS blocks and one
+// thread per block reads each tile's flags: a rebuild without a re-sort then costs a
+// short launch, not ~4,000 blocks of 256 threads each reading the flags.
+constexpr int RESORT_BLOCKS = 152 * 8;
+
 __global__ void __launch_bounds__(TILE_P) k_permute(const SysDev* __restrict__ sysv,
-                                                    const Tile* __restrict__ tiles,
+                                                    const Tile* __restrict__ tiles, int ntiles,
                                                     GroupCtl* ctl) {
-  const Tile t = tiles[blockIdx.x];
-  const SysDev& s = sysv[t.sys];
-  count(s, t, ctl);
-  if (!sorting(s) || threadIdx.x >= t.count) return;
-  const int k = t.first + threadIdx.x, n = s.n;
-  const int o = s.members[k];
-  for (int a = 0; a < 3; ++a) {
-    s.x_alt[a * n + k] = s.x[a * n + o];
-    s.v_alt[a * n + k] = s.v[a * n + o];
-    s.img_alt[a * n + k] = s.img[a * n + o];
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
+  __shared__ int srt;
+  for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
+    const Tile t = tiles[b];
+    const SysDev& s = sysv[t.sys];
+    __syncthreads();   // the previous tile's srt has been read
+    if (threadIdx.x == 0) {
+      if (t.first == 0) atomicAdd(&s.flags->launches, 1ull);
+      srt = sorting(s);   // one read of the flags per tile, not one per thread
+    }
+    __syncthreads();
+    if (!srt || threadIdx.x >= t.count) continue;
+    const int k = t.first + threadIdx.x, n = s.n;
+    const int o = s.members[k];
+    for (int a = 0; a < 3; ++a) {
+      s.x_alt[a * n + k] = s.x[a * n + o];
+      s.v_alt[a * n + k] = s.v[a * n + o];
+      s.img_alt[a * n + k] = s.img[a * n + o];
+    }
+    s.type_alt[k] = s.type[o];
+    s.tag_alt[k] = s.tag[o];
+    s.q_alt[k] = q_at(s, step_of(s.flags))[o];
   }
-  s.type_alt[k] = s.type[o];
-  s.tag_alt[k] = s.tag[o];
-  s.q_alt[k] = q_at(s, step_of(s.flags))[o];
 }
 
 __global__ void __launch_bounds__(TILE_P) k_copyback(const SysDev* __restrict__ sysv,
-                                                     const Tile* __restrict__ tiles,
+                                                     const Tile* __restrict__ tiles, int ntiles,
                                                      GroupCtl* ctl) {
-  const Tile t = tiles[blockIdx.x];
-  const SysDev& s = sysv[t.sys];
-  count(s, t, ctl);
-  if (!sorting(s) || threadIdx.x >= t.count) return;
-  const int k = t.first + threadIdx.x, n = s.n;
-  double xr[3];
-  for (int a = 0; a < 3; ++a) {
-    const double xq = s.x_alt[a * n + k];
-    s.x[a * n + k] = xq;
-    s.v[a * n + k] = s.v_alt[a * n + k];
-    s.img[a * n + k] = s.img_alt[a * n + k];
-    xr[a] = xq * (s.L[a] * (1.0 / 4294967296.0));
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
+  __shared__ int srt;
+  for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
+    const Tile t = tiles[b];
+    const SysDev& s = sysv[t.sys];
+    __syncthreads();   // the previous tile's srt has been read
+    if (threadIdx.x == 0) {
+      if (t.first == 0) atomicAdd(&s.flags->launches, 1ull);
+      srt = sorting(s);   // one read of the flags per tile, not one per thread
+    }
+    __syncthreads();
+    if (!srt || threadIdx.x >= t.count) continue;
+    const int k = t.first + threadIdx.x, n = s.n;
+    double xr[3];
+    for (int a = 0; a < 3; ++a) {
+      const double xq = s.x_alt[a * n + k];
+      s.x[a * n + k] = xq;
+      s.v[a * n + k] = s.v_alt[a * n + k];
+      s.img[a * n + k] = s.img_alt[a * n + k];
+      xr[a] = xq * (s.L[a] * (1.0 / 4294967296.0));
+    }
+    const int ty = s.type_alt[k];
+    s.type[k] = ty;
+    const int tg = s.tag_alt[k];
+    s.tag[k] = tg;
+    s.rtag[tg] = k;
+    const long long step = step_of(s.flags);
+    q_at(s, step)[k] = s.q_alt[k];
+    s.members[k] = k;
+    s.rmember[k] = k;
+    if (s.precision == GBMD_FP64)
+      p64_at(s, step)[k] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
   }
-  const int ty = s.type_alt[k];
-  s.type[k] = ty;
-  const int tg = s.tag_alt[k];
-  s.tag[k] = tg;
-  s.rtag[tg] = k;
-  const long long step = step_of(s.flags);
-  q_at(s, step)[k] = s.q_alt[k];
-  s.members[k] = k;
-  s.rmember[k] = k;
-  if (s.precision == GBMD_FP64)
-    p64_at(s, step)[k] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
 }
 
 // ---- staged force tiles: the window of every aligned 2x2x2 block of cells ----
@@ -345,7 +371,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   const SysDev& s = sysv[t.sys];
   count(s, t, ctl);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (!rebuilding(s) || s.tree || w >= t.count) return;
+  if (!block_rebuilding(s) || s.tree || w >= t.count) return;
   const int nt = s.ntypes;
   // r_list^2 (1 -+ band) per type pair (FP32)
   __shared__ float thr_lo[CELLS_PER_TILE][MAXT2], thr_hi[CELLS_PER_TILE][MAXT2];
@@ -513,7 +539,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
       // kept (it lies in the box); selfabs is its ring position.
       int fill = 0, tested = 0, selfabs = -1;
       auto test32 = [&](int hb) {
-        unsigned mlo = 0, mhi = 0;
+        unsigned mlo = 0u, mhi = 0u;
 #pragma unroll
         for (int k = 0; k < 32; k += 2) {
           const float2 X = *reinterpret_cast<const float2*>(&cxs[w][hb + k]);
@@ -648,8 +674,15 @@ SIMPLE_CALL(bin_call, k_bin, TILE_P)
 SIMPLE_CALL(scan_call, k_scan, SCAN_THREADS)
 SIMPLE_CALL(scatter_call, k_scatter, TILE_P)
 SIMPLE_CALL(cellsort_call, k_cellsort, CELLS_PER_TILE * 32)
-SIMPLE_CALL(permute_call, k_permute, TILE_P)
-SIMPLE_CALL(copyback_call, k_copyback, TILE_P)
+#define RESORT_CALL(name, kern)                                                  \
+  KernelCall name(const SysDev* d, const Tile* tl, int ntiles, GroupCtl* ctl) { \
+    KernelCall k = make_call((void*)kern, std::min(ntiles, RESORT_BLOCKS), TILE_P, 0); \
+    put(k, d); put(k, tl); put(k, ntiles); put(k, ctl);                            \
+    return k;                                                                    \
+  }
+RESORT_CALL(permute_call, k_permute)
+RESORT_CALL(copyback_call, k_copyback)
+#undef RESORT_CALL
 SIMPLE_CALL(blocks_call, k_blocks, 256)
 #undef SIMPLE_CALL
 

@@ -15,6 +15,13 @@ constexpr float NL_BAND = 1e-5f;
 __device__ __forceinline__ bool rebuilding(const SysDev& s) {
   return ((const volatile Flags*)s.flags)->do_rebuild != 0;
 }
+// the same, read by one thread and shared with the block (every thread must call it)
+__device__ __forceinline__ bool block_rebuilding(const SysDev& s) {
+  __shared__ int r;
+  if (threadIdx.x == 0) r = rebuilding(s);
+  __syncthreads();
+  return r != 0;
+}
 // launch counters: per system (the block of its first tile) and per group
 __device__ __forceinline__ void count(const SysDev& s, const Tile& t, GroupCtl* ctl) {
   if (threadIdx.x == 0 && t.first == 0) atomicAdd(&s.flags->launches, 1ull);
