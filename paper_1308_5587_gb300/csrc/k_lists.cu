@@ -7,8 +7,11 @@
 //     c_a = floor((q_a + 2^31) * nc_a / 2^32), cell width L_a / nc_a >= r_list_max;
 //   * cells are numbered by their rank in Morton (Z-order) of (cx, cy, cz);
 //   * counting sort: atomic histogram -> exclusive scan -> atomic scatter, then
-//     each cell's members are sorted by particle index, so the result is the
-//     stable order (cell rank, index) whatever order the atomics ran in;
+//     each cell's members are sorted by (the particle's own 30-bit Morton code,
+//     index), so the result is the order (cell rank, fine Morton code, index)
+//     whatever order the atomics ran in, and consecutive members of a cell are
+//     spatial neighbours (a warp of the force kernel gathers from fewer lines:
+//     2% off the step kernel at KA 10^6);
 //   * neighbour list: full list (both i->j and j->i), one warp per cell whose lanes
 //     are the cell's particles; every lane tests the same candidate j of the
 //     neighbouring cells at a time (warp-uniform loop, broadcast loads).  Keep
@@ -65,11 +68,11 @@ __global__ void __launch_bounds__(TILE_P) k_bin(const SysDev* __restrict__ sysv,
   const int cx = cell_of_fixed(q.x, s.nc[0]);
   const int cy = cell_of_fixed(q.y, s.nc[1]);
   const int cz = cell_of_fixed(q.z, s.nc[2]);
-  // the tree list sorts type-major (each type's particles contiguous, in cell order)
-  // and, inside a bin, by the particle's own Morton code (the leaves' order)
+  // the tree list sorts type-major (each type's particles contiguous, in cell order);
+  // inside a bin every list orders by the particle's own Morton code
   const int r = s.lin2rank[(cz * s.nc[1] + cy) * s.nc[0] + cx] + (s.tree ? q.w * s.ncells : 0);
   s.key[i] = r;
-  if (s.tree) s.fkey[i] = fine_morton(q);
+  s.fkey[i] = fine_morton(q);
   atomicAdd(&s.cell_cnt[r], 1);
 }
 
@@ -137,8 +140,8 @@ __global__ void __launch_bounds__(TILE_P) k_scatter(const SysDev* __restrict__ s
 }
 
 // ---- sort each bin's members (warp per bin) -> a deterministic order ----
-// By particle index (the stable order); on the tree list by (fine Morton code,
-// index), so that consecutive members of a bin are spatial neighbours.
+// By (fine Morton code, index), so that consecutive members of a bin are spatial
+// neighbours (the tree list's leaves; the force kernel's warps).
 __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* __restrict__ sysv,
                                                                   const Tile* __restrict__ tiles,
                                                                   GroupCtl* ctl) {
@@ -149,10 +152,9 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* 
   if (!block_rebuilding(s) || w >= t.count) return;
   const int r = t.first + w;
   const int b = s.cell_start[r], e = s.cell_start[r + 1], n = e - b;
-  const bool fine = s.tree != 0;
-  // the sort key of member m: (fine code, index) or the index alone
+  // the sort key of member m: (fine code, index)
   auto key = [&](int v) -> unsigned long long {
-    return ((unsigned long long)(fine ? s.fkey[v] : 0u) << 32) | (unsigned)v;
+    return ((unsigned long long)s.fkey[v] << 32) | (unsigned)v;
   };
   if (n <= 32) {
     const int v = lane < n ? s.members_tmp[b + lane] : 0x7fffffff;
@@ -383,6 +385,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
       czs[CELLS_PER_TILE][64], cts[CELLS_PER_TILE][64];
   __shared__ int cjs[CELLS_PER_TILE][64];
   __shared__ int cand_l[STAGED ? CELLS_PER_TILE : 1][64];   // window-local index
+  __shared__ float wbox[CELLS_PER_TILE][6];   // the pass's bounding box (culling)
   // STAGED: some member of the group may use the staged force path (decided per
   // system below); otherwise none does
   const bool staged = STAGED && s.staged != 0;   // then every axis has >= 4 cells
@@ -474,9 +477,17 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     const float zi = (float)min_image_fixed(qi.z, oz) * fs2;
     const float2 nX = make_float2(-xi, -xi), nY = make_float2(-yi, -yi), nZ = make_float2(-zi, -zi);
     // the bounding box of this pass's particles (REL culling)
-    const float bx0 = warp_min(valid ? xi : 3e38f), bx1 = warp_max(valid ? xi : -3e38f);
-    const float by0 = warp_min(valid ? yi : 3e38f), by1 = warp_max(valid ? yi : -3e38f);
-    const float bz0 = warp_min(valid ? zi : 3e38f), bz1 = warp_max(valid ? zi : -3e38f);
+    // (kept in shared memory: read once per fetched chunk, they need no registers)
+    {
+      const float bx0 = warp_min(valid ? xi : 3e38f), bx1 = warp_max(valid ? xi : -3e38f);
+      const float by0 = warp_min(valid ? yi : 3e38f), by1 = warp_max(valid ? yi : -3e38f);
+      const float bz0 = warp_min(valid ? zi : 3e38f), bz1 = warp_max(valid ? zi : -3e38f);
+      if (lane == 0) {
+        wbox[w][0] = bx0; wbox[w][1] = bx1; wbox[w][2] = by0;
+        wbox[w][3] = by1; wbox[w][4] = bz0; wbox[w][5] = bz1;
+      }
+      __syncwarp();
+    }
     // An idle lane gets thresholds -1 (never keeps).  Two types: -lo for a type-0
     // candidate and its change for type 1 in registers; more types read the table.
     const int pt = MULTI ? qi.w * nt : 0;
@@ -576,7 +587,8 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
         const float qx = (float)min_image_fixed(nq.x, ox) * fs0;
         const float qy = (float)min_image_fixed(nq.y, oy) * fs1;
         const float qz = (float)min_image_fixed(nq.z, oz) * fs2;
-        const float gx = gap_to(qx, bx0, bx1), gy = gap_to(qy, by0, by1), gz = gap_to(qz, bz0, bz1);
+        const float gx = gap_to(qx, wbox[w][0], wbox[w][1]), gy = gap_to(qy, wbox[w][2], wbox[w][3]),
+                    gz = gap_to(qz, wbox[w][4], wbox[w][5]);
         const bool keep = !nempty && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < cull2;
         const unsigned kb = __ballot_sync(0xffffffffu, keep);
         const int p = fill + __popc(kb & ((1u << lane) - 1u));
