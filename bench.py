@@ -23,8 +23,9 @@ the timed region.  An end-to-end loop through the public API with host buffers
 
 Beside the headline (skipped with --no-sub): the arithmetic peaks measured by the
 library's probe, the LJ 64k fluid in mixed precision and on the plain FP64 path
-with the FP64 pipe roofline ("vs FP64 plain path"), and the 256-replica batched
-ensemble against that plain FP64 single-system loop.
+with the FP64 pipe roofline ("vs FP64 plain path"), the 256-replica batched
+ensemble against that plain FP64 single-system loop, and a short served stream
+(p50/p99 latency).
 
 --impl reference times the CPU oracle (FP64, O(N^2)) on this host's cores on a
 bounded sample of the same workload.  Under torchrun each rank runs its own
@@ -603,6 +604,34 @@ def sub_records(torch, args, out, stream, dist, local):
                                     "what": "plain FP64 path, LJ 64k single system (above)"}
     b["batched_over_fp64_loop"] = round(b["value"] / fp64["value"], 2)
     out["batched"] = b
+    out["served"] = served_short(torch, stream, local, fp64["value"])
+
+
+def served_short(torch, stream, local, fp64_value):
+    """A short served stream beside the headline: the served trace's shape (Poisson
+    arrivals at 50/s, N log-uniform in [256, 200000], rho, T as the batch) with 48
+    requests and their step counts scaled by 1/20 (U{50..2500}), under the 150 GB
+    budget.  The full trace (1,000 requests, U{1000..50000} steps) runs for minutes:
+    `--workload serve --requests 1000`."""
+    from paper_1308_5587_gb300 import serve, workloads as wl
+    be = serve.GpuBackend("mixed", stream=stream.cuda_stream, cuda_device=local)
+    serve.Scheduler(be, 1 << 40).run([serve.Request(-1, 0.0, 50, 4000,
+                                                    dict(n=4000, rho=0.8, T=1.0, seed=1))])
+    trace = wl.request_trace(48, 50.0, seed=wl.BASE_SEED + 2000, steps_lo=50, steps_hi=2500)
+    summ = serve.Scheduler(be, int(150e9), max_quantum=2000).run(serve.requests_from_trace(trace))
+    be.close()
+    done = [r for r in summ.records if r.finished is not None]
+    value = summ.particle_steps / summ.makespan
+    return {"value": value, "unit": UNIT,
+            "workload": "served stream: 48 requests, Poisson 50/s, N log-uniform [256, 200000], "
+                        "rho U(0.7, 0.9), T U(0.8, 1.5), steps U{50..2500} (the served "
+                        "trace's steps / 20), budget 150 GB, mixed",
+            "latency_s": {"p50": summ.p50, "p99": summ.p99, "mean": summ.mean,
+                          "completed": len(done),
+                          "rejected": sum(r.rejected for r in summ.records)},
+            "makespan_s": summ.makespan, "quanta": summ.quanta,
+            "peak_resident_bytes": summ.peak_resident_bytes,
+            "over_fp64_single_system_loop": round(value / fp64_value, 2)}
 
 
 # ---------------------------------------------------------------------------
@@ -650,8 +679,10 @@ def run_batch(torch, replicas, steps, warmup, stream, dist, local, autotune=True
     step_ms, _, launches = timed_steps(torch, stepper, steps, warmup, None, stream, dist,
                                        region=True)
     clk = clocks.stop()
-    _, force_ms, _ = timed_steps(torch, stepper, min(steps, 500), 3, None, stream, dist,
-                                 force_events=True)
+    step1_ms, force_ms, _ = timed_steps(torch, stepper, min(steps, 500), 3, None, stream, dist,
+                                        force_events=True)
+    med = float(np.median(step1_ms))
+    reb = step1_ms[step1_ms > 1.8 * med]
     infos = [x.info() for x in systems]
     tune = (infos[0]["threads_per_particle"], infos[0]["force_block"])
     th = [x.thermo() for x in systems[:4]]
@@ -673,6 +704,10 @@ def run_batch(torch, replicas, steps, warmup, stream, dist, local, autotune=True
             "n": n, "replicas": len(ws), "threads_per_particle": tune[0],
             "force_block": tune[1], "autotuned": bool(autotune),
             "l2": "inputs larger than L2",
+            "step_split": {"median_step_ms": round(med, 5), "rebuild_steps": int(reb.size),
+                           "of_steps": int(step1_ms.size),
+                           "rebuild_step_ms_mean": round(float(reb.mean()), 5) if reb.size
+                           else None},
             "timed_iteration": "all K steps of every replica between one event pair, as one "
                                "gbmd_batch_step(K) call (16-step CUDA graphs)",
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
