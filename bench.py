@@ -739,8 +739,8 @@ def batch_arm(args):
                       "l2": r["l2"], "timed_iteration": r["timed_iteration"],
                       "threads_per_particle": r["threads_per_particle"],
                       "force_block": r["force_block"]},
-           "tps": r["tps"], "roofline": r["roofline"], "clocks": r["clocks"],
-           "gpu_launches": r["gpu_launches"], "e2e": None}
+           "tps": r["tps"], "roofline": r["roofline"], "step_split": r["step_split"],
+           "clocks": r["clocks"], "gpu_launches": r["gpu_launches"], "e2e": None}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -359,12 +359,13 @@ __device__ __forceinline__ unsigned push_sign(unsigned m, float v) {
   return __funnelshift_l(__float_as_uint(v), m, 1);
 }
 
-// REL: every axis has at least 3 cells, so a candidate's coordinate relative to the
-// cell centre, taken in [-L/2, L/2), is already its minimum image with respect to
-// every particle of the cell (|d| < r_list <= w and the particle lies within w/2
-// of the centre).  With 1 or 2 cells on an axis a neighbour may sit on either side,
-// so the !REL variant keeps fixed-point coordinates and takes the minimum image
-// per test.
+// With at least 3 cells on every axis, a candidate's coordinate relative to the cell
+// centre, taken in [-L/2, L/2), is already its minimum image with respect to every
+// particle of the cell (|d| < r_list <= w and the particle lies within w/2 of the
+// centre).  With 1 or 2 cells on an axis a neighbour may sit on either side, so such
+// a system keeps fixed-point coordinates and takes the minimum image per test.  The
+// REL instance serves launches whose systems all have 3 cells per axis; the other
+// decides per system.
 template <bool MULTI, bool REL, bool STAGED>
 __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* __restrict__ sysv,
                                                                   const Tile* __restrict__ tiles,
@@ -413,6 +414,10 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   const int lo1 = nc1 >= 3 ? -1 : 0, n1 = nc1 >= 3 ? 3 : nc1;
   const int lo2 = nc2 >= 3 ? -1 : 0, n2 = nc2 >= 3 ? 3 : nc2;
   const int nsc = n0 * n1 * n2;   // <= 27
+  // REL: every system of the launch has >= 3 cells per axis; otherwise each system
+  // takes the relative-coordinate path when it has them (warp-uniform: a warp is one
+  // cell of one system), so a batch with one small member builds the others fast
+  const bool rel = REL || (nc0 >= 3 && nc1 >= 3 && nc2 >= 3);
   const int own_sc = -lo0 + n0 * (-lo1 + n1 * -lo2);   // the cell's own stencil slot
   int sc_start = 0, sc_cnt = 0, sc_woff = 0;
   if (lane < nsc) {
@@ -543,7 +548,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     };
 
     fetch(lane);
-    if (REL) {
+    if (rel) {
       // Kept candidates go into a ring of 64 slots in stream order; every time 32
       // are waiting they are tested together (a full, unrolled chunk), so culling
       // saves tests and not only stores.  The particle's own candidate is always
