@@ -56,14 +56,46 @@ __device__ __forceinline__ unsigned fine_morton(const int4& q) {
          (spread10(((unsigned)q.z ^ 0x80000000u) >> 22) << 2);
 }
 
+// The per-particle rebuild kernels (bin, scatter, permute, copyback) walk the tile
+// table with a grid of at most WALK_BLOCKS blocks.  Warp 0 reads, for up to 32 of the
+// block's next tiles at once, whether their system does this work (and counts the
+// launch at each system's first tile); the block then works on those tiles only.  In
+// a batch where a few members rebuild, the others' tiles then cost one parallel read,
+// not a block each.
+constexpr int WALK_BLOCKS = 152 * 8;
+
+template <typename Active, typename Work>
+__device__ __forceinline__ void walk_tiles(const SysDev* __restrict__ sysv,
+                                           const Tile* __restrict__ tiles, int ntiles,
+                                           GroupCtl* ctl, Active active, Work work) {
+  __shared__ int act[32];
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
+  for (int b0 = blockIdx.x; b0 < ntiles; b0 += 32 * gridDim.x) {
+    __syncthreads();   // the previous round's act[] has been read
+    if (threadIdx.x < 32) {
+      const int b = b0 + threadIdx.x * gridDim.x;
+      int a = 0;
+      if (b < ntiles) {
+        const Tile t = tiles[b];
+        const SysDev& s = sysv[t.sys];
+        if (t.first == 0) atomicAdd(&s.flags->launches, 1ull);
+        a = active(s) ? 1 : 0;
+      }
+      act[threadIdx.x] = a;
+    }
+    __syncthreads();
+    for (int l = 0; l < 32; ++l) {
+      const int b = b0 + l * gridDim.x;
+      if (b >= ntiles) break;
+      if (!act[l]) continue;
+      const Tile t = tiles[b];
+      if ((int)threadIdx.x < t.count) work(sysv[t.sys], t.first + (int)threadIdx.x);
+    }
+  }
+}
+
 // ---- binning + histogram ----
-__global__ void __launch_bounds__(TILE_P) k_bin(const SysDev* __restrict__ sysv,
-                                                const Tile* __restrict__ tiles, GroupCtl* ctl) {
-  const Tile t = tiles[blockIdx.x];
-  const SysDev& s = sysv[t.sys];
-  count(s, t, ctl);
-  if (!block_rebuilding(s) || threadIdx.x >= t.count) return;
-  const int i = t.first + threadIdx.x;
+__device__ __forceinline__ void bin_one(const SysDev& s, int i) {
   const int4 q = q_at(s, step_of(s.flags))[i];
   const int cx = cell_of_fixed(q.x, s.nc[0]);
   const int cy = cell_of_fixed(q.y, s.nc[1]);
@@ -74,6 +106,12 @@ __global__ void __launch_bounds__(TILE_P) k_bin(const SysDev* __restrict__ sysv,
   s.key[i] = r;
   s.fkey[i] = fine_morton(q);
   atomicAdd(&s.cell_cnt[r], 1);
+}
+
+__global__ void __launch_bounds__(TILE_P) k_bin(const SysDev* __restrict__ sysv,
+                                                const Tile* __restrict__ tiles, int ntiles,
+                                                GroupCtl* ctl) {
+  walk_tiles(sysv, tiles, ntiles, ctl, [](const SysDev& s) { return rebuilding(s); }, bin_one);
 }
 
 // ---- exclusive scan of the bin counts (one block per system) ----
@@ -128,15 +166,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SysDev* __restrict_
 
 // ---- scatter particle indices into their cells (unordered within a cell) ----
 __global__ void __launch_bounds__(TILE_P) k_scatter(const SysDev* __restrict__ sysv,
-                                                    const Tile* __restrict__ tiles,
+                                                    const Tile* __restrict__ tiles, int ntiles,
                                                     GroupCtl* ctl) {
-  const Tile t = tiles[blockIdx.x];
-  const SysDev& s = sysv[t.sys];
-  count(s, t, ctl);
-  if (!block_rebuilding(s) || threadIdx.x >= t.count) return;
-  const int i = t.first + threadIdx.x;
-  const int p = atomicAdd(&s.cell_cursor[s.key[i]], 1);
-  s.members_tmp[p] = i;
+  walk_tiles(sysv, tiles, ntiles, ctl, [](const SysDev& s) { return rebuilding(s); },
+             [](const SysDev& s, int i) {
+               const int p = atomicAdd(&s.cell_cursor[s.key[i]], 1);
+               s.members_tmp[p] = i;
+             });
 }
 
 // ---- sort each bin's members (warp per bin) -> a deterministic order ----
@@ -178,76 +214,54 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* 
 }
 
 // ---- re-sort: gather every per-particle array into cell order ----
-// Both kernels run at every rebuild and do work only when the system re-sorts, so
-// they walk the tile table with a grid of at most RESORT_BLOCKS blocks and one
-// thread per block reads each tile's flags: a rebuild without a re-sort then costs a
-// short launch, not ~4,000 blocks of 256 threads each reading the flags.
-constexpr int RESORT_BLOCKS = 152 * 8;
+// Both kernels run at every rebuild and do work only when the system re-sorts (the
+// tile walker makes that cheap when it does not).
+__device__ __forceinline__ void permute_one(const SysDev& s, int k) {
+  const int n = s.n;
+  const int o = s.members[k];
+  for (int a = 0; a < 3; ++a) {
+    s.x_alt[a * n + k] = s.x[a * n + o];
+    s.v_alt[a * n + k] = s.v[a * n + o];
+    s.img_alt[a * n + k] = s.img[a * n + o];
+  }
+  s.type_alt[k] = s.type[o];
+  s.tag_alt[k] = s.tag[o];
+  s.q_alt[k] = q_at(s, step_of(s.flags))[o];
+}
+
+__device__ __forceinline__ void copyback_one(const SysDev& s, int k) {
+  const int n = s.n;
+  double xr[3];
+  for (int a = 0; a < 3; ++a) {
+    const double xq = s.x_alt[a * n + k];
+    s.x[a * n + k] = xq;
+    s.v[a * n + k] = s.v_alt[a * n + k];
+    s.img[a * n + k] = s.img_alt[a * n + k];
+    xr[a] = xq * (s.L[a] * (1.0 / 4294967296.0));
+  }
+  const int ty = s.type_alt[k];
+  s.type[k] = ty;
+  const int tg = s.tag_alt[k];
+  s.tag[k] = tg;
+  s.rtag[tg] = k;
+  const long long step = step_of(s.flags);
+  q_at(s, step)[k] = s.q_alt[k];
+  s.members[k] = k;
+  s.rmember[k] = k;
+  if (s.precision == GBMD_FP64)
+    p64_at(s, step)[k] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
+}
 
 __global__ void __launch_bounds__(TILE_P) k_permute(const SysDev* __restrict__ sysv,
                                                     const Tile* __restrict__ tiles, int ntiles,
                                                     GroupCtl* ctl) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
-  __shared__ int srt;
-  for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
-    const Tile t = tiles[b];
-    const SysDev& s = sysv[t.sys];
-    __syncthreads();   // the previous tile's srt has been read
-    if (threadIdx.x == 0) {
-      if (t.first == 0) atomicAdd(&s.flags->launches, 1ull);
-      srt = sorting(s);   // one read of the flags per tile, not one per thread
-    }
-    __syncthreads();
-    if (!srt || threadIdx.x >= t.count) continue;
-    const int k = t.first + threadIdx.x, n = s.n;
-    const int o = s.members[k];
-    for (int a = 0; a < 3; ++a) {
-      s.x_alt[a * n + k] = s.x[a * n + o];
-      s.v_alt[a * n + k] = s.v[a * n + o];
-      s.img_alt[a * n + k] = s.img[a * n + o];
-    }
-    s.type_alt[k] = s.type[o];
-    s.tag_alt[k] = s.tag[o];
-    s.q_alt[k] = q_at(s, step_of(s.flags))[o];
-  }
+  walk_tiles(sysv, tiles, ntiles, ctl, [](const SysDev& s) { return sorting(s); }, permute_one);
 }
 
 __global__ void __launch_bounds__(TILE_P) k_copyback(const SysDev* __restrict__ sysv,
                                                      const Tile* __restrict__ tiles, int ntiles,
                                                      GroupCtl* ctl) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
-  __shared__ int srt;
-  for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
-    const Tile t = tiles[b];
-    const SysDev& s = sysv[t.sys];
-    __syncthreads();   // the previous tile's srt has been read
-    if (threadIdx.x == 0) {
-      if (t.first == 0) atomicAdd(&s.flags->launches, 1ull);
-      srt = sorting(s);   // one read of the flags per tile, not one per thread
-    }
-    __syncthreads();
-    if (!srt || threadIdx.x >= t.count) continue;
-    const int k = t.first + threadIdx.x, n = s.n;
-    double xr[3];
-    for (int a = 0; a < 3; ++a) {
-      const double xq = s.x_alt[a * n + k];
-      s.x[a * n + k] = xq;
-      s.v[a * n + k] = s.v_alt[a * n + k];
-      s.img[a * n + k] = s.img_alt[a * n + k];
-      xr[a] = xq * (s.L[a] * (1.0 / 4294967296.0));
-    }
-    const int ty = s.type_alt[k];
-    s.type[k] = ty;
-    const int tg = s.tag_alt[k];
-    s.tag[k] = tg;
-    s.rtag[tg] = k;
-    const long long step = step_of(s.flags);
-    q_at(s, step)[k] = s.q_alt[k];
-    s.members[k] = k;
-    s.rmember[k] = k;
-    if (s.precision == GBMD_FP64)
-      p64_at(s, step)[k] = make_double4_32a(xr[0], xr[1], xr[2], __longlong_as_double(ty));
-  }
+  walk_tiles(sysv, tiles, ntiles, ctl, [](const SysDev& s) { return sorting(s); }, copyback_one);
 }
 
 // ---- staged force tiles: the window of every aligned 2x2x2 block of cells ----
@@ -687,19 +701,19 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     put(k, d); put(k, tl); put(k, ctl);                                          \
     return k;                                                                    \
   }
-SIMPLE_CALL(bin_call, k_bin, TILE_P)
 SIMPLE_CALL(scan_call, k_scan, SCAN_THREADS)
-SIMPLE_CALL(scatter_call, k_scatter, TILE_P)
 SIMPLE_CALL(cellsort_call, k_cellsort, CELLS_PER_TILE * 32)
-#define RESORT_CALL(name, kern)                                                  \
+#define WALK_CALL(name, kern)                                                  \
   KernelCall name(const SysDev* d, const Tile* tl, int ntiles, GroupCtl* ctl) { \
-    KernelCall k = make_call((void*)kern, std::min(ntiles, RESORT_BLOCKS), TILE_P, 0); \
+    KernelCall k = make_call((void*)kern, std::min(ntiles, WALK_BLOCKS), TILE_P, 0);   \
     put(k, d); put(k, tl); put(k, ntiles); put(k, ctl);                            \
     return k;                                                                    \
   }
-RESORT_CALL(permute_call, k_permute)
-RESORT_CALL(copyback_call, k_copyback)
-#undef RESORT_CALL
+WALK_CALL(bin_call, k_bin)
+WALK_CALL(scatter_call, k_scatter)
+WALK_CALL(permute_call, k_permute)
+WALK_CALL(copyback_call, k_copyback)
+#undef WALK_CALL
 SIMPLE_CALL(blocks_call, k_blocks, 256)
 #undef SIMPLE_CALL
 
