@@ -345,6 +345,13 @@ __global__ void __launch_bounds__(256) k_blocks(const SysDev* __restrict__ sysv,
 // candidates between the two go through the FP64 decision.  Hits are appended in
 // candidate order either way, so a row is the same whichever variant built it.
 constexpr int NL_TYPE_SHIFT = 30;
+// REL rows of the global list: the final hit masks of up to NL_SEG tested chunks wait
+// in shared memory, with their candidates in a ring of NL_JR indices, and each lane
+// then appends all its hits of the segment in one loop (NL_JR >= 32 NL_SEG + 63: the
+// tested segment plus the candidates compacted but not yet tested)
+constexpr int NL_SEG = 14;
+constexpr int NL_JR = 512;
+static_assert(NL_JR >= 32 * NL_SEG + 63 && (NL_JR & (NL_JR - 1)) == 0, "segment ring");
 // a culled candidate is at least this factor beyond the largest r_list^2 (1 + band)
 // from the warp's box, far above the FP32 rounding of the box distance
 constexpr float NL_CULL_MARGIN = 1e-4f;
@@ -401,6 +408,8 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   __shared__ int cjs[CELLS_PER_TILE][64];
   __shared__ int cand_l[STAGED ? CELLS_PER_TILE : 1][64];   // window-local index
   __shared__ float wbox[CELLS_PER_TILE][6];   // the pass's bounding box (culling)
+  __shared__ int jring[CELLS_PER_TILE][NL_JR];             // j of kept candidates (REL)
+  __shared__ unsigned hmask[CELLS_PER_TILE][NL_SEG][32];   // a lane's hits per chunk
   // STAGED: some member of the group may use the staged force path (decided per
   // system below); otherwise none does
   const bool staged = STAGED && s.staged != 0;   // then every axis has >= 4 cells
@@ -531,7 +540,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
     // band).  The band is decided in FP64 first; then the hits are appended in
     // candidate order (the row does not depend on how r^2 was rounded).  Entries
     // past the capacity are counted, not stored.
-    auto append_hits = [&](unsigned mlo, unsigned mhi, int hb) {
+    auto resolve_band = [&](unsigned mlo, unsigned mhi, int hb) -> unsigned {
       unsigned band = mhi & ~mlo;
       while (band) {
         const int k = __clz(band);
@@ -541,6 +550,10 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
         const int p = MULTI ? pt + ((unsigned)cw >> NL_TYPE_SHIFT) : 0;
         if (!exact_within(s, i, j, rl2d[w][p])) mhi &= ~(0x80000000u >> k);
       }
+      return mhi;
+    };
+    auto append_hits = [&](unsigned mlo, unsigned mhi, int hb) {
+      mhi = resolve_band(mlo, mhi, hb);
       if (!staged) {
         const int* __restrict__ cj = &cjs[w][hb];
         while (mhi) {
@@ -559,6 +572,52 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
           ++cnt;
         }
       }
+    };
+
+    // The deferred append of a segment (REL, global rows): chunk c's final mask of
+    // this lane is hmask[c], bit c of nzb says it is not empty.  Hits are taken in
+    // (chunk, candidate) order, four to a 16-byte store of the row's next slot group
+    // (a short last group is padded with its first entry, which lies past the count
+    // unless the next segment overwrites it).
+    int4* __restrict__ nl4 = reinterpret_cast<int4*>(s.nl) + i_row;
+    unsigned nzb = 0;
+    int nseg = 0, seg0 = 0;
+    auto flush = [&]() {
+      unsigned m = 0;
+      int c = 0;
+      auto next = [&](int& j) -> bool {
+        if (m == 0u) {
+          if (nzb == 0u) return false;
+          c = __ffs(nzb) - 1;
+          nzb &= nzb - 1u;
+          m = hmask[w][c][lane];
+        }
+        const int k = __clz(m);
+        m &= 0x7fffffffu >> k;
+        j = jring[w][(seg0 + c * 32 + k) & (NL_JR - 1)];
+        return true;
+      };
+      int j0, j1, j2, j3;
+      while ((cnt & 3) != 0 && next(j0)) {   // complete the group the last segment began
+        if (cnt < cap) s.nl[((size_t)(cnt >> 2) * stride + i_row) * 4 + (cnt & 3)] = j0;
+        ++cnt;
+      }
+      for (;;) {
+        if (!next(j0)) break;
+        int r = 1;
+        j1 = j2 = j3 = j0;
+        if (next(j1)) {
+          ++r;
+          if (next(j2)) {
+            ++r;
+            if (next(j3)) ++r;
+          }
+        }
+        if (cnt < cap) nl4[(size_t)(cnt >> 2) * stride] = make_int4(j0, j1, j2, j3);
+        cnt += r;
+        if (r < 4) break;
+      }
+      nseg = 0;
     };
 
     fetch(lane);
@@ -599,7 +658,15 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
           mlo &= ~(0x80000000u >> rs);
           mhi &= ~(0x80000000u >> rs);
         }
-        append_hits(mlo, mhi, hb);
+        if (staged) {
+          append_hits(mlo, mhi, hb);
+        } else {
+          if (nseg == 0) seg0 = tested;
+          const unsigned m = resolve_band(mlo, mhi, hb);
+          hmask[w][nseg][lane] = m;
+          nzb |= (m != 0u ? 1u : 0u) << nseg;
+          if (++nseg == NL_SEG) flush();
+        }
       };
       for (int cb = 0; cb < total; cb += 32) {
         // relative coordinates; cull against the box and compact the survivors
@@ -618,6 +685,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
           czs[w][sl] = qz;
           cts[w][sl] = (float)(((unsigned)nq.w >> NL_TYPE_SHIFT) & 1u);
           cjs[w][sl] = nq.w;
+          jring[w][p & (NL_JR - 1)] = nq.w & ((1 << NL_TYPE_SHIFT) - 1);
           if (STAGED) cand_l[w][sl] = nloc;
         }
         const int rs = self_pos - cb;
@@ -644,6 +712,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
         test32(tested & 63);
         __syncwarp();
       }
+      if (nseg > 0) flush();
     } else {
       for (int cb = 0; cb < total; cb += 32) {
         cxs[w][lane] = __int_as_float(nq.x);
