@@ -748,7 +748,7 @@ size_t footprint_of(const gbmd_desc* d, const Geometry& g) {
   if (d->precision == GBMD_FP64) b += n * 32 * 2;   // p64 (two buffers)
   b += n * (d->precision == GBMD_FP64 ? 32 : 16);   // force
   b += n * 4 + round_up(n, 32) * 4 * (size_t)g.cap;  // nn, nl (ELL4)
-  b += n * 4 * 5 + (size_t)(g.nbins + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;   // cells, keys
+  b += n * (4 * 5 + 16) + (size_t)(g.nbins + 1) * 4 * 3 + (size_t)g.ncells * 4 * 2;   // cells, keys
   if (d->nlist == GBMD_NLIST_TREE)   // tree boxes and arrival counters (<= n + 4 ntypes
     b += (n + 4 * (size_t)d->ntypes) * (sizeof(TreeBox) + 4) + n * 16;  // nodes), leaves
   b += (size_t)((g.nc[0] + 1) / 2) * ((g.nc[1] + 1) / 2) * ((g.nc[2] + 1) / 2) *
@@ -968,6 +968,7 @@ int create_impl(const gbmd_desc* d, gbmd_system** out, bool device) {
   A((void**)&h.x_alt, N * 24); A((void**)&h.v_alt, N * 24); A((void**)&h.img_alt, N * 12);
   A((void**)&h.type_alt, N * 4); A((void**)&h.tag_alt, N * 4); A((void**)&h.q_alt, N * 16);
   A((void**)&h.fkey, N * 4);   // fine Morton keys: the order inside a cell
+  A((void**)&h.cpos, N * 16);  // positions in cell order (the list build's candidates)
   A((void**)&h.thermo, 16 * 8);
   A((void**)&h.nh, 4 * 8);
   if (tree) {

@@ -126,6 +126,7 @@ struct SysDev {
   unsigned* tree_arrive;   // per node: children arrived during the build (reset to 0)
   unsigned* fkey;          // [N] the particle's fine Morton code at the last build (every
                            // system: the order inside a cell)
+  int4* cpos;              // [N] position shadow of member m (cell order) at the last build
   int4* tree_q;            // [N] the leaves' particles in leaf order: (x, y, z, index)
   // the list kernel visits the types in decreasing order of their expected query work
   // (sum over t of n_t r_list(type, t)^3): launch positions tree_qpos[k] .. belong to

@@ -105,7 +105,10 @@ __device__ __forceinline__ void bin_one(const SysDev& s, int i) {
   const int r = s.lin2rank[(cz * s.nc[1] + cy) * s.nc[0] + cx] + (s.tree ? q.w * s.ncells : 0);
   s.key[i] = r;
   s.fkey[i] = fine_morton(q);
-  atomicAdd(&s.cell_cnt[r], 1);
+  // consecutive particles mostly share a bin: one atomic per distinct bin of the warp
+  const unsigned am = __activemask();
+  const unsigned peers = __match_any_sync(am, r);
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s.cell_cnt[r], __popc(peers));
 }
 
 __global__ void __launch_bounds__(TILE_P) k_bin(const SysDev* __restrict__ sysv,
@@ -132,10 +135,19 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SysDev* __restrict_
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nc = s.nbins;
-  for (int base = 0; base < nc; base += SCAN_THREADS) {
-    const int c = base + threadIdx.x;
-    const int v = c < nc ? s.cell_cnt[c] : 0;
-    int x = v;
+  // four bins per thread (one 16-byte load where all four exist; the buffers come
+  // from cudaMalloc, so 16-byte aligned)
+  for (int base = 0; base < nc; base += 4 * SCAN_THREADS) {
+    const int c = base + 4 * threadIdx.x;
+    int v[4];
+    if (c + 3 < nc) {
+      const int4 q = *reinterpret_cast<const int4*>(s.cell_cnt + c);
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+      for (int k = 0; k < 4; ++k) v[k] = c + k < nc ? s.cell_cnt[c + k] : 0;
+    }
+    const int v4 = v[0] + v[1] + v[2] + v[3];
+    int x = v4;
     for (int o = 1; o < 32; o <<= 1) {
       int y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
@@ -151,11 +163,24 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SysDev* __restrict_
       warp_tot[lane] = w;   // inclusive over warps
     }
     __syncthreads();
-    const int excl = carry + (wid ? warp_tot[wid - 1] : 0) + x - v;
-    if (c < nc) {
-      s.cell_start[c] = excl;
-      s.cell_cursor[c] = excl;
-      s.cell_cnt[c] = 0;   // ready for the next build
+    int e[4];
+    e[0] = carry + (wid ? warp_tot[wid - 1] : 0) + x - v4;
+    e[1] = e[0] + v[0];
+    e[2] = e[1] + v[1];
+    e[3] = e[2] + v[2];
+    if (c + 3 < nc) {
+      const int4 q = make_int4(e[0], e[1], e[2], e[3]);
+      *reinterpret_cast<int4*>(s.cell_start + c) = q;
+      *reinterpret_cast<int4*>(s.cell_cursor + c) = q;
+      *reinterpret_cast<int4*>(s.cell_cnt + c) = make_int4(0, 0, 0, 0);   // next build
+    } else {
+      for (int k = 0; k < 4; ++k) {
+        if (c + k < nc) {
+          s.cell_start[c + k] = e[k];
+          s.cell_cursor[c + k] = e[k];
+          s.cell_cnt[c + k] = 0;
+        }
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) carry += warp_tot[31];
@@ -170,8 +195,17 @@ __global__ void __launch_bounds__(TILE_P) k_scatter(const SysDev* __restrict__ s
                                                     GroupCtl* ctl) {
   walk_tiles(sysv, tiles, ntiles, ctl, [](const SysDev& s) { return rebuilding(s); },
              [](const SysDev& s, int i) {
-               const int p = atomicAdd(&s.cell_cursor[s.key[i]], 1);
-               s.members_tmp[p] = i;
+               // one atomic per distinct bin of the warp; the peers take consecutive
+               // slots after their leader's (the order inside a bin is fixed later)
+               const int r = s.key[i];
+               const int lane = threadIdx.x & 31;
+               const unsigned am = __activemask();
+               const unsigned peers = __match_any_sync(am, r);
+               const int leader = __ffs(peers) - 1;
+               int base = 0;
+               if (lane == leader) base = atomicAdd(&s.cell_cursor[r], __popc(peers));
+               base = __shfl_sync(am, base, leader);
+               s.members_tmp[base + __popc(peers & ((1u << lane) - 1u))] = i;
              });
 }
 
@@ -192,6 +226,10 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* 
   auto key = [&](int v) -> unsigned long long {
     return ((unsigned long long)s.fkey[v] << 32) | (unsigned)v;
   };
+  // the members' positions are copied in the same order: the list build then reads
+  // a cell's candidates contiguously, however far the particles have drifted from
+  // the order of the last re-sort
+  const int4* __restrict__ qv = q_at(s, step_of(s.flags));
   if (n <= 32) {
     const int v = lane < n ? s.members_tmp[b + lane] : 0x7fffffff;
     const unsigned long long kv = lane < n ? key(v) : ~0ull;
@@ -200,6 +238,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* 
     if (lane < n) {
       s.members[b + rk] = v;
       s.rmember[v] = b + rk;
+      s.cpos[b + rk] = qv[v];
     }
   } else {
     for (int m = lane; m < n; m += 32) {
@@ -209,6 +248,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32) k_cellsort(const SysDev* 
       for (int k = 0; k < n; ++k) rk += key(s.members_tmp[b + k]) < kv;
       s.members[b + rk] = v;
       s.rmember[v] = b + rk;
+      s.cpos[b + rk] = qv[v];
     }
   }
 }
@@ -400,11 +440,11 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   // r_list^2 (1 -+ band) per type pair (FP32)
   __shared__ float thr_lo[CELLS_PER_TILE][MAXT2], thr_hi[CELLS_PER_TILE][MAXT2];
   __shared__ double rl2d[CELLS_PER_TILE][MAXT2];
-  // the chunk of 32 candidates, one array per component so that candidates k and
-  // k + 1 load as one FP32x2 operand: x, y, z (relative to the cell centre; raw
-  // fixed point without REL), the type as 0/1, and j | type << 30
-  __shared__ __align__(8) float cxs[CELLS_PER_TILE][64], cys[CELLS_PER_TILE][64],
-      czs[CELLS_PER_TILE][64], cts[CELLS_PER_TILE][64];
+  // the chunk of candidates: x, y, z (relative to the cell centre; raw fixed point
+  // without REL) and the type as 0/1, candidates 2m and 2m + 1 interleaved as
+  // cxy[m] = (x, x', y, y') and czt[m] = (z, z', t, t') so that a pair loads as two
+  // 16-byte words of FP32x2 operands; and j | type << 30
+  __shared__ float4 cxy[CELLS_PER_TILE][32], czt[CELLS_PER_TILE][32];
   __shared__ int cjs[CELLS_PER_TILE][64];
   __shared__ int cand_l[STAGED ? CELLS_PER_TILE : 1][64];   // window-local index
   __shared__ float wbox[CELLS_PER_TILE][6];   // the pass's bounding box (culling)
@@ -465,9 +505,23 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   const int b = s.cell_start[r], e = s.cell_start[r + 1];
   const int cap = s.cap;
   const int* __restrict__ members = s.members;
-  const int4* __restrict__ qv = q_at(s, step_of(s.flags));
+  const int4* __restrict__ cpos = s.cpos;   // member m's position (written by the cell sort)
   const bool two = !MULTI || nt <= 2;
   __syncwarp();
+
+  auto put_cand = [&](int sl, float x, float y, float z, float t) {
+    float* a = reinterpret_cast<float*>(&cxy[w][sl >> 1]) + (sl & 1);
+    float* c = reinterpret_cast<float*>(&czt[w][sl >> 1]) + (sl & 1);
+    a[0] = x;
+    a[2] = y;
+    c[0] = z;
+    c[2] = t;
+  };
+  // component a (0 x, 1 y, 2 z) of slot sl
+  auto cand_comp = [&](int sl, int a) -> float {
+    const float* b = reinterpret_cast<const float*>(a < 2 ? &cxy[w][sl >> 1] : &czt[w][sl >> 1]);
+    return b[(a == 1 ? 2 : 0) + (sl & 1)];
+  };
 
   // candidate c of the flattened stream into registers (every lane runs every
   // shuffle); written to the chunk arrays by stage() once the previous chunk is done
@@ -491,7 +545,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
       return;
     }
     const int j = members[st + (c - ex)];
-    const int4 qj = qv[j];
+    const int4 qj = cpos[st + (c - ex)];
     nq = make_int4(qj.x, qj.y, qj.z, j | (qj.w << NL_TYPE_SHIFT));
   };
 
@@ -499,7 +553,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
   for (int ibase = b; ibase < e; ibase += 32) {
     const bool valid = ibase + lane < e;
     const int i = valid ? members[ibase + lane] : -1;
-    const int4 qi = valid ? qv[i] : make_int4(0, 0, 0, 0);
+    const int4 qi = valid ? cpos[ibase + lane] : make_int4(0, 0, 0, 0);
     const float xi = (float)min_image_fixed(qi.x, ox) * fs0;
     const float yi = (float)min_image_fixed(qi.y, oy) * fs1;
     const float zi = (float)min_image_fixed(qi.z, oz) * fs2;
@@ -631,14 +685,14 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
         unsigned mlo = 0u, mhi = 0u;
 #pragma unroll
         for (int k = 0; k < 32; k += 2) {
-          const float2 X = *reinterpret_cast<const float2*>(&cxs[w][hb + k]);
-          const float2 Y = *reinterpret_cast<const float2*>(&cys[w][hb + k]);
-          const float2 Z = *reinterpret_cast<const float2*>(&czs[w][hb + k]);
+          const float4 A = cxy[w][(hb + k) >> 1];
+          const float4 B = czt[w][(hb + k) >> 1];
+          const float2 X = make_float2(A.x, A.y), Y = make_float2(A.z, A.w), Z = make_float2(B.x, B.y);
           float2 nlo;   // -r_list^2 (1 - band) of each candidate's type pair
           if (!MULTI) {
             nlo = nl0;
           } else if (two) {
-            nlo = __ffma2_rn(*reinterpret_cast<const float2*>(&cts[w][hb + k]), ndl, nl0);
+            nlo = __ffma2_rn(make_float2(B.z, B.w), ndl, nl0);
           } else {
             const unsigned t0 = (unsigned)cjs[w][hb + k] >> NL_TYPE_SHIFT;
             const unsigned t1 = (unsigned)cjs[w][hb + k + 1] >> NL_TYPE_SHIFT;
@@ -680,10 +734,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
         const int p = fill + __popc(kb & ((1u << lane) - 1u));
         if (keep) {
           const int sl = p & 63;
-          cxs[w][sl] = qx;
-          cys[w][sl] = qy;
-          czs[w][sl] = qz;
-          cts[w][sl] = (float)(((unsigned)nq.w >> NL_TYPE_SHIFT) & 1u);
+          put_cand(sl, qx, qy, qz, (float)(((unsigned)nq.w >> NL_TYPE_SHIFT) & 1u));
           cjs[w][sl] = nq.w;
           jring[w][p & (NL_JR - 1)] = nq.w & ((1 << NL_TYPE_SHIFT) - 1);
           if (STAGED) cand_l[w][sl] = nloc;
@@ -702,10 +753,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
       if (fill > tested) {   // the last, partial chunk: pad it with far-away slots
         if (lane >= fill - tested) {
           const int sl = (tested + lane) & 63;
-          cxs[w][sl] = 1e18f;
-          cys[w][sl] = 1e18f;
-          czs[w][sl] = 1e18f;
-          cts[w][sl] = 0.0f;
+          put_cand(sl, 1e18f, 1e18f, 1e18f, 0.0f);
           cjs[w][sl] = 0;
         }
         __syncwarp();
@@ -715,9 +763,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
       if (nseg > 0) flush();
     } else {
       for (int cb = 0; cb < total; cb += 32) {
-        cxs[w][lane] = __int_as_float(nq.x);
-        cys[w][lane] = __int_as_float(nq.y);
-        czs[w][lane] = __int_as_float(nq.z);
+        put_cand(lane, __int_as_float(nq.x), __int_as_float(nq.y), __int_as_float(nq.z), 0.0f);
         cjs[w][lane] = nq.w;
         if (STAGED) cand_l[w][lane] = nloc;
         const int m = min(32, total - cb);
@@ -728,9 +774,9 @@ __global__ void __launch_bounds__(CELLS_PER_TILE * 32, 3) k_nlist(const SysDev* 
           float r2 = 3e38f;
           int p = 0;
           if (k < m) {
-            const float dx = (float)min_image_fixed(qi.x, __float_as_int(cxs[w][k])) * fs0;
-            const float dy = (float)min_image_fixed(qi.y, __float_as_int(cys[w][k])) * fs1;
-            const float dz = (float)min_image_fixed(qi.z, __float_as_int(czs[w][k])) * fs2;
+            const float dx = (float)min_image_fixed(qi.x, __float_as_int(cand_comp(k, 0))) * fs0;
+            const float dy = (float)min_image_fixed(qi.y, __float_as_int(cand_comp(k, 1))) * fs1;
+            const float dz = (float)min_image_fixed(qi.z, __float_as_int(cand_comp(k, 2))) * fs2;
             r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const unsigned ct = (unsigned)cjs[w][k] >> NL_TYPE_SHIFT;
             p = !MULTI ? 0 : two ? (int)(ct & 1) : (int)ct;
