@@ -127,6 +127,43 @@ def test_neighbor_sets_match_brute_force(prec):
         s.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_neighbor_sets_of_dense_cells_span_several_segments(prec):
+    """r_buff 1.5 at rho 1.2: cells 4 sigma wide hold ~77 particles (three passes of a
+    warp), about 1,200 candidates per pass survive the culling (several segments of 14
+    tested chunks, appended with rows left mid slot group between segments), ~320
+    neighbours per particle, and exactly 3 cells per axis (the smallest grid of the
+    relative-coordinate path).  Neighbour sets equal the brute-force pairs and the
+    forces match the oracle, before and after a rebuild from moved positions."""
+    base = wl.lj_fluid(4000, 1.2, 1.0, seed=46)
+    w = wl.Workload(base.pos, base.vel, base.types, base.box, base.pairs, r_buff=1.5)
+    assert int(w.box[0] // (float(w.pairs.rcut.max()) + 1.5)) == 3
+    s = gbmd.System.from_workload(w, precision=prec)
+    for rnd in range(2):
+        pos = s.state()[0]
+        counts, idx = s.neighbors(cap=512)
+        assert counts.max() < 512 and counts.mean() > 250
+        rl = w.pairs.rcut + w.r_buff
+        pairs, r = oracle.neighbors(pos, w.box, w.types, rl)
+        rlp = rl[w.types[pairs[:, 0]], w.types[pairs[:, 1]]]
+        ok = np.abs(r - rlp) > 1e-9
+        ref = {(int(a), int(b)) for a, b in pairs[ok]}
+        band = {(int(a), int(b)) for a, b in pairs[~ok]}
+        mine = set()
+        for i in range(w.n):
+            row = idx[i, :counts[i]]
+            assert np.all(np.diff(row) > 0)
+            mine.update((min(i, int(j)), max(i, int(j))) for j in row)
+        assert counts.sum() == 2 * len(mine)
+        assert mine - band == ref
+        F = s.forces()
+        Fo, *_ = oracle.forces(pos, w.box, w.types, w.pairs.as_dict())
+        assert rel_l2(F, Fo) <= (1e-12 if prec == "fp64" else 1e-5)
+        pos2 = pos + np.random.default_rng(10 + rnd).normal(scale=0.1, size=pos.shape)
+        s.set_state(pos2, s.state()[1])
+    s.close()
+
+
 def test_trajectory_plain_fp64_4000_100_steps():
     """The plain FP64 configuration: N=4,000 LJ, 100 NVE steps, vs the oracle."""
     w = wl.plain_fp64_4k()
