@@ -18,8 +18,8 @@
 //     j != i with r^2 < r_list,ij^2 (strict), r_list,ij = r_cut,ij + r_buff.  The
 //     test runs in FP32 on the fixed-point difference; candidates within a relative
 //     band of 1e-5 of r_list^2 are decided again in FP64 with the same operations
-//     (and rounding) as the brute-force reference definition, and appended after
-//     the other hits of their chunk of 32 candidates.
+//     (and rounding) as the brute-force reference definition.  Hits are appended in
+//     candidate order, so a row does not depend on how r^2 was rounded.
 #include <algorithm>
 
 #include "launch.cuh"
@@ -365,21 +365,22 @@ __global__ void __launch_bounds__(256) k_blocks(const SysDev* __restrict__ sysv,
 
 // ---- neighbour list: one warp per cell ----
 // Lanes are the cell's particles (up to 32 at a time).  The candidates -- the
-// members of the stencil cells in (dz, dy, dx) cell order and index order within
-// a cell, flattened into one stream -- pass through a per-warp shared-memory
-// buffer 32 at a time, each converted once into FP32 coordinates relative to the
-// centre of the warp's cell (the fixed-point difference takes care of the
-// periodic wrap) plus j | type << 30; the next chunk is loaded while the current
-// one is tested.  Every lane then tests the broadcast candidate against its own
-// particle with packed FP32x2 arithmetic (no integer work per test) and appends
-// hits to its row, so each row holds its neighbours in (stencil cell, index)
-// order.  Candidates within a relative band of 1e-5 of r_list^2 are decided in
-// FP64 as the definition does (the FP32 error is below 2e-6 relative).
+// members of the stencil cells in (dz, dy, dx) cell order and member order within
+// a cell, flattened into one stream, their positions read from the copy in cell
+// order that the cell sort wrote -- pass through a per-warp shared-memory buffer
+// 32 at a time, each converted once into FP32 coordinates relative to the centre
+// of the warp's cell (the fixed-point difference takes care of the periodic wrap)
+// plus j | type << 30; the next chunk is loaded while the current one is tested.
+// Every lane then tests the broadcast candidate against its own particle with
+// packed FP32x2 arithmetic (no integer work per test) and appends hits to its row,
+// so each row holds its neighbours in (stencil cell, member) order.  Candidates
+// within a relative band of 1e-5 of r_list^2 are decided in FP64 as the definition
+// does (the FP32 error is below 2e-6 relative).
 //
 // With at least 3 cells per axis (REL) each chunk is first culled: a candidate
 // farther than the largest r_list from the bounding box of the warp's particles
-// cannot be anyone's neighbour, and the survivors are compacted (about a quarter
-// of the stencil lies outside that reach).  The test yields two bit masks per
+// cannot be anyone's neighbour, and the survivors are compacted (at KA density
+// 44% of the stencil lies outside that reach).  The test yields two bit masks per
 // lane -- r^2 below r_list^2 (1 - band), a neighbour, and below r_list^2 (1 + band)
 // -- so appending a hit is a load of its index and a store, and only the rare
 // candidates between the two go through the FP64 decision.  Hits are appended in
