@@ -297,7 +297,10 @@ int gbmd_get_per_particle(gbmd_system *s, double *energy, double *virial);
 int gbmd_get_state(gbmd_system *s, double *pos, double *vel, int32_t *image, int64_t *step);
 
 /* Resume: replace positions (any image), velocities and image counts (NULL image
- * = zeros) and the step counter; rebuilds the lists and recomputes forces. */
+ * = zeros) and the step counter; rebuilds the lists and recomputes forces.  Host
+ * buffers, tag order, the types kept.  A non-finite position or velocity gives
+ * GBMD_ERR_BAD_ARG and leaves the system as it was (checked on the device before
+ * anything is replaced).  GBMD_ERR_STATE for a member of a batch. */
 int gbmd_set_state(gbmd_system *s, const double *pos, const double *vel, const int32_t *image,
                    int64_t step);
 

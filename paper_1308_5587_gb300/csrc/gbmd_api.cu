@@ -1497,17 +1497,23 @@ int gbmd_set_state(gbmd_system* s, const double* pos, const double* vel, const i
   if (s->batch) return fail(GBMD_ERR_STATE, "remove the system from its batch first");
   RET(sync_system(s));
   const size_t N = (size_t)s->h.n;
-  for (size_t i = 0; i < 3 * N; ++i)
-    if (!std::isfinite(pos[i]) || !std::isfinite(vel[i])) return fail(GBMD_ERR_BAD_ARG, "non-finite state");
-  // types in tag order, gathered from the internal arrays
-  std::vector<int> types(N), tags(N);
   cudaStream_t st = cur_stream(s);
-  CK(cudaMemcpyAsync(types.data(), s->h.type, N * 4, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(tags.data(), s->h.tag, N * 4, cudaMemcpyDeviceToHost, st));
+  Group* g = s->own;
+  RET(sync_layout(g));
+  // The new state goes to the staging buffers; its finiteness and the current types
+  // in tag order are taken there on the device, and nothing of the system is
+  // replaced unless every value is finite.
+  CK(cudaMemcpyAsync(s->d_pos, pos, N * 24, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->d_vel, vel, N * 24, cudaMemcpyHostToDevice, st));
+  if (image) CK(cudaMemcpyAsync(s->d_img, image, N * 12, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(s->d_misc, 0, 4, st));
+  CK(launch(prep_state_call(g->d_desc, g->d_tp, g->ntp, s->d_pos, s->d_vel, s->d_type, s->d_misc),
+            st));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, s->d_misc, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  std::vector<int> by_tag(N);
-  for (size_t k = 0; k < N; ++k) by_tag[tags[k]] = types[k];
-  return load_state(s, pos, vel, by_tag.data(), image, false, step);
+  if (bad) return fail(GBMD_ERR_BAD_ARG, "non-finite state");
+  return load_state(s, s->d_pos, s->d_vel, s->d_type, image ? s->d_img : nullptr, true, step);
 }
 
 int gbmd_get_neighbors(gbmd_system* s, int32_t* counts, int32_t* idx, int64_t cap) {

@@ -57,6 +57,25 @@ __global__ void __launch_bounds__(256) k_thermo(const SysDev* __restrict__ sysv,
 // ---------------------------------------------------------------------------
 // import: tag-order row-major host layout -> internal planar arrays (identity order)
 // ---------------------------------------------------------------------------
+// set_state, before anything is replaced: whether the new positions and velocities
+// (tag order, in the staging buffers) are all finite, and the current types in tag
+// order for the import
+__global__ void __launch_bounds__(TILE_P) k_prep_state(const SysDev* __restrict__ sysv,
+                                                       const Tile* __restrict__ tiles,
+                                                       const double* __restrict__ pos,
+                                                       const double* __restrict__ vel,
+                                                       int* __restrict__ type_by_tag, int* bad) {
+  const Tile t = tiles[blockIdx.x];
+  const SysDev& s = sysv[t.sys];
+  if (threadIdx.x >= t.count) return;
+  const int g = t.first + threadIdx.x;   // a tag
+  bool ok = true;
+  for (int a = 0; a < 3; ++a)
+    ok = ok && isfinite(pos[3 * (size_t)g + a]) && isfinite(vel[3 * (size_t)g + a]);
+  if (!ok) atomicExch(bad, 1);
+  type_by_tag[g] = s.type[s.rtag[g]];
+}
+
 __global__ void __launch_bounds__(TILE_P) k_import(const SysDev* __restrict__ sysv,
                                                    const Tile* __restrict__ tiles,
                                                    const double* __restrict__ pos,
@@ -282,6 +301,13 @@ KernelCall import_call(const SysDev* d, const Tile* tiles_p, int ntiles, const d
                        const double* vel, const int* type, const int* image) {
   KernelCall k = mk((void*)k_import, ntiles, TILE_P);
   put(k, d); put(k, tiles_p); put(k, pos); put(k, vel); put(k, type); put(k, image);
+  return k;
+}
+
+KernelCall prep_state_call(const SysDev* d, const Tile* tiles_p, int ntiles, const double* pos,
+                           const double* vel, int* type_by_tag, int* bad) {
+  KernelCall k = mk((void*)k_prep_state, ntiles, TILE_P);
+  put(k, d); put(k, tiles_p); put(k, pos); put(k, vel); put(k, type_by_tag); put(k, bad);
   return k;
 }
 

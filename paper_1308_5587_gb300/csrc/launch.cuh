@@ -73,6 +73,8 @@ constexpr int STAGED_BLOCK = 256;
 // thermo reduction (K7), one block per system
 KernelCall thermo_call(const SysDev* d, const Tile* tiles_s, int nsys, GroupCtl* ctl);
 // import row-major tag-order staging -> internal arrays; export the reverse
+KernelCall prep_state_call(const SysDev* d, const Tile* tiles_p, int ntiles, const double* pos,
+                           const double* vel, int* type_by_tag, int* bad);
 KernelCall import_call(const SysDev* d, const Tile* tiles_p, int ntiles, const double* pos,
                        const double* vel, const int* type, const int* image);
 KernelCall export_call(const SysDev* d, const Tile* tiles_p, int ntiles, double* pos,

@@ -268,6 +268,44 @@ def test_checkpoint_resume():
     b.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_set_state_keeps_types_and_refuses_non_finite_input(prec):
+    """set_state on a binary mixture whose particles have been re-sorted (tags no
+    longer equal to internal indices): the types stay with their tags, so the forces
+    at the new state match the oracle's with the original types.  A NaN or inf in
+    the new positions or velocities is refused (BAD_ARG) and leaves the system as it
+    was: same state, same forces, and it keeps stepping."""
+    w = wl.lj_fluid(3000, 1.2, 1.0, seed=82, binary=True, r_buff=0.3)
+    s = gbmd.System.from_workload(w, precision=prec, sort_period=10)
+    s.step(40)
+    assert s.info()["n_sorts"] >= 2
+    rng = np.random.default_rng(3)
+    pos2 = w.pos + rng.normal(scale=0.05, size=w.pos.shape)
+    vel2 = rng.normal(size=w.vel.shape)
+    s.set_state(pos2, vel2, None, 7)
+    pos, vel, img, step = s.state()
+    assert step == 7
+    assert np.abs(mi(pos - pos2, w.box)).max() < 1e-9
+    F = s.forces()
+    Fo, *_ = oracle.forces(pos, w.box, w.types, w.pairs.as_dict())
+    assert rel_l2(F, Fo) <= (1e-12 if prec == "fp64" else 1e-5)
+    before = s.state()
+    for bad_pos, bad_vel in ((np.nan, 0.0), (0.0, np.inf), (-np.inf, 0.0)):
+        p3, v3 = pos2.copy(), vel2.copy()
+        p3[1234, 1] += bad_pos
+        v3[17, 2] += bad_vel
+        with pytest.raises(gbmd.GbmdError) as e:
+            s.set_state(p3, v3, None, 9)
+        assert e.value.status == "BAD_ARG"
+        after = s.state()
+        for x, y in zip(before, after):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+    assert np.array_equal(s.forces(), F)
+    s.step(10)
+    assert s.state()[3] == 17
+    s.close()
+
+
 def test_deterministic_reruns():
     w = wl.lj_fluid(5000, 0.84, 1.2, seed=91)
     out = []
