@@ -239,7 +239,7 @@ def recorded_traffic(workload: str, precision: str):
 # ---------------------------------------------------------------------------
 
 def timed_steps(torch, s, K: int, W: int, flush, stream, dist, force_events: bool = False,
-                region: bool = False):
+                region: bool = False, counts: dict = None):
     """W warm-up steps, then K steps each bracketed by events on the stream; returns
     per-step milliseconds, per-force-kernel milliseconds (force_events: event nodes
     around the force kernel inside the step graph, which add a few microseconds to
@@ -261,7 +261,8 @@ def timed_steps(torch, s, K: int, W: int, flush, stream, dist, force_events: boo
     s.sync()
     barrier(dist)
     torch.cuda.synchronize()
-    l0 = s.info()["kernel_launches"]
+    i0 = s.info()
+    l0 = i0["kernel_launches"]
     whole = region and flush is None and not force_events
     if whole:
         ev[0][0].record(stream)
@@ -279,7 +280,10 @@ def timed_steps(torch, s, K: int, W: int, flush, stream, dist, force_events: boo
     torch.cuda.synchronize()
     barrier(dist)
     s.sync()
-    l1 = s.info()["kernel_launches"]
+    i1 = s.info()
+    l1 = i1["kernel_launches"]
+    if counts is not None and "n_rebuilds" in i1:
+        counts["rebuilds"] = int(i1["n_rebuilds"] - i0["n_rebuilds"])
     if whole:
         step_ms = np.full(K, ev[0][0].elapsed_time(ev[0][3]) / K)
     else:
@@ -391,8 +395,9 @@ def run_system(torch, w, precision, sort_period, stream, dist, local, flush, ste
     step_ms, _, launches = timed_steps(torch, s, steps, warmup, flush, stream, dist,
                                        region=True)
     clk = clocks.stop() if clocks else None
+    cnt = {}
     step1_ms, force_ms, _ = timed_steps(torch, s, min(steps, 1000), 3, flush, stream, dist,
-                                        force_events=True)
+                                        force_events=True, counts=cnt)
     info = s.info()
     th = s.thermo()
     s.close()
@@ -400,10 +405,11 @@ def run_system(torch, w, precision, sort_period, stream, dist, local, flush, ste
     t_local = float(step_ms.sum()) / 1e3
     t_max = reduce_scalar(dist, t_local, "max")
     units = reduce_scalar(dist, w.n * steps, "sum")
-    # steps that rebuilt the lists stand out: well above the median step (second pass,
-    # single-step graphs with the force-kernel event nodes)
+    # the steps that rebuilt the lists (as many as the device counted in the second
+    # pass, single-step graphs with the force-kernel event nodes) are its slowest
     med = float(np.median(step1_ms))
-    reb = step1_ms[step1_ms > 1.8 * med]
+    k_reb = min(cnt.get("rebuilds", 0), step1_ms.size)
+    reb = np.sort(step1_ms)[step1_ms.size - k_reb:] if k_reb else step1_ms[:0]
     split = {"median_step_ms": round(med, 5),
              "rebuild_steps": int(reb.size), "of_steps": int(step1_ms.size),
              "rebuild_step_ms_mean": round(float(reb.mean()), 5) if reb.size else None,
