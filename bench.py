@@ -478,15 +478,16 @@ def probe_peaks(torch, local):
 def fp64_roofline(n, nbar, force_ms, peaks, r_cut, r_list):
     """Roofline of the FP64 step kernel against the measured FP64 FMA rate.  FP64
     operations (each add, multiply or fused multiply-add counts one) from the
-    kernel's arithmetic: per listed pair the displacement (3) and r^2 (3); per pair
-    inside r_cut one reciprocal (counted as the DFMA slots it takes, measured by the
-    probe), r^-6 (2), the force factor (3) and the three accumulations (3); per
-    particle the integration's kicks, drifts, rounding and FP64 shadow (13).  The
-    share of listed pairs inside r_cut is the uniform-fluid estimate
-    (r_cut / r_list)^3."""
+    kernel's arithmetic: a listed pair beyond r_cut is rejected by an FP32 test on
+    the fixed-point shadow and takes none; a pair inside r_cut takes the
+    displacement (3), r^2 (3), one reciprocal (counted as the DFMA slots it takes,
+    measured by the probe), r^-6 (2), the force factor (3) and the three
+    accumulations (3); per particle the integration's kicks, drifts, rounding and
+    FP64 shadow (13).  The share of listed pairs inside r_cut is the uniform-fluid
+    estimate (r_cut / r_list)^3."""
     rcp = peaks["drcp_in_dfma_slots"]
     f_cut = (r_cut / r_list) ** 3
-    per_pair = 6 + f_cut * (8 + rcp)
+    per_pair = f_cut * (14 + rcp)
     ops = n * (nbar * per_pair + 13)
     achieved = ops / (force_ms * 1e-3)
     peak = peaks["dfma"]["ops_per_s"]

@@ -424,8 +424,9 @@ int gbmd_abi_version(void);
  * path's full-FP64 throughput on a V100).  `kind` selects the operation:
  *   GBMD_PROBE_DFMA  FP64 fused multiply-add,
  *   GBMD_PROBE_FFMA  FP32 fused multiply-add,
- *   GBMD_PROBE_DRCP  FP64 correctly rounded reciprocal (one per pair in the FP64
- *                    force kernel).
+ *   GBMD_PROBE_DRCP  the FP64 reciprocal of the FP64 force kernel (one per pair
+ *                    inside r_cut: hardware approximation plus one third-order
+ *                    refinement, within 1 ulp of the correctly rounded value).
  * One launch over every SM of the current device (8 blocks of 256 threads per
  * SM, 8 independent chains per thread, `iters` >= 1 rounds) on `stream`
  * (cudaStream_t or NULL), after an untimed warm-up launch; *ops receives the

@@ -34,6 +34,7 @@
 #pragma once
 #include "launch.cuh"
 #include "step_core.cuh"
+#include "fp64_math.cuh"
 
 namespace gbmd {
 
@@ -137,16 +138,21 @@ __device__ __forceinline__ void eval_f32x2(const float2 r2, const PairF& Pa, con
   }
 }
 
+// The FP64 path's FP32 pre-test keeps every pair with r^2 < r_cut^2 (1 + 1e-5): its
+// FP32 r^2 (int32 difference, two roundings) is within 3e-7 relative of the FP64
+// one, and the fixed-point shadow within 2^-32 L of the FP64 position.
+constexpr float FP64_PRETEST_MARGIN = 1.0f + 1e-5f;
+
 // FP64, one neighbour
 template <int EVAL, bool EV>
 __device__ __forceinline__ double eval_f64(double r2, const PairD& P, double& v) {
   if constexpr (EVAL == EVAL_LJ) {
-    const double r2i = __drcp_rn(r2);
+    const double r2i = rcp_f64(r2);
     const double r6i = r2i * r2i * r2i;
     if (EV) v = fma(r6i, fma(P.p3, r6i, -P.p4), -P.shift);
     return r2i * r6i * fma(P.p0, r6i, -P.p1);
   } else if constexpr (EVAL == EVAL_MIE) {
-    const double r2i = __drcp_rn(r2);
+    const double r2i = rcp_f64(r2);
     const double x = P.p0 * r2i;   // (sigma / r)^2
     const double tn = pow(x, P.p1), tm = pow(x, P.p2);
     if (EV) v = P.p3 * (tn - tm) - P.shift;
@@ -227,7 +233,12 @@ __device__ __forceinline__ void force_body(const SysDev* __restrict__ sysv,
   __shared__ PairD tabd[SMEM_TAB ? MAXT2 : 1];
   if (SMEM_TAB) {
     for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
-      if (PREC == GBMD_MIXED) tabf[k] = s.pf[k]; else tabd[k] = s.pd[k];
+      if (PREC == GBMD_MIXED) {
+        tabf[k] = s.pf[k];
+      } else {   // FP64: the FP32 cut for the pre-test, and the FP64 coefficients
+        tabf[k] = s.pf[k];
+        tabd[k] = s.pd[k];
+      }
     }
     __syncthreads();
   }
@@ -313,6 +324,11 @@ __device__ __forceinline__ void force_body(const SysDev* __restrict__ sysv,
     const double4_32a* __restrict__ pv = p64_at(s, step);
     const double4_32a pi = pv[i];
     const int ti = (int)__double_as_longlong(pi.w);
+    // the FP32 pre-test reads the fixed-point shadow of the same positions
+    const int4* __restrict__ qv = q_at(s, step);
+    const int4 qi = qv[i];
+    const float fs0 = s.fscale[0], fs1 = s.fscale[1], fs2 = s.fscale[2];
+    const float cut0 = s.pf[0].rc2 * FP64_PRETEST_MARGIN;
     const double L0 = s.L[0], L1 = s.L[1], L2 = s.L[2];
     const int h0 = __double2hiint(s.halfL[0]), h1 = __double2hiint(s.halfL[1]),
               h2 = __double2hiint(s.halfL[2]);
@@ -325,10 +341,24 @@ __device__ __forceinline__ void force_body(const SysDev* __restrict__ sysv,
       const int k0 = gg << 2;
       const int jj[4] = {jc.x, jc.y, jc.z, jc.w};
       double4_32a pp[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) pp[u] = pv[k0 + u < n ? jj[u] : i];   // own slot: unused
+      int4 qq[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
+        const int j = k0 + u < n ? jj[u] : i;   // own slot: unused
+        pp[u] = pv[j];
+        qq[u] = __ldg(qv + j);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        // FP32 pre-test on the fixed-point difference (the exact minimum image): a
+        // pair beyond r_cut by more than the margin skips the FP64 work, which it
+        // would not pass; every other pair is decided in FP64 below
+        const float ex = (float)min_image_fixed(qi.x, qq[u].x) * fs0;
+        const float ey = (float)min_image_fixed(qi.y, qq[u].y) * fs1;
+        const float ez = (float)min_image_fixed(qi.z, qq[u].z) * fs2;
+        const float r2f = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        const float cut = MT ? tabf[ti * nt + qq[u].w].rc2 * FP64_PRETEST_MARGIN : cut0;
+        if (!(k0 + u < n) || !(r2f < cut)) continue;
         const double4_32a pj = pp[u];
         double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         // minimum image: |d| < L; the test on the high words is exact except within

@@ -6,11 +6,12 @@
 // the pipe, not latency, sets the rate:
 //   PROBE_DFMA: x <- fma(x, a, b) in FP64          (one FP64 multiply-add)
 //   PROBE_FFMA: x <- fmaf(x, a, b) in FP32         (one FP32 multiply-add)
-//   PROBE_DRCP: x <- __drcp_rn(x) in FP64          (the reciprocal the FP64 pair
+//   PROBE_DRCP: x <- rcp_f64(x) in FP64            (the reciprocal the FP64 pair
 //                                                   force takes once per pair)
 // The grid is the SM count times 8 blocks of 256 threads.  Each thread stores the
 // sum of its chains, so the compiler cannot drop them.
 #include "launch.cuh"
+#include "fp64_math.cuh"
 
 namespace gbmd {
 
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(PROBE_BLOCK) k_probe(double* __restrict__ sink
 #pragma unroll
       for (int c = 0; c < PROBE_CH; ++c) {
         if constexpr (KIND == GBMD_PROBE_DFMA) x[c] = fma(x[c], a, b);
-        else x[c] = __drcp_rn(x[c]);
+        else x[c] = rcp_f64(x[c]);
       }
     }
 #pragma unroll

@@ -22,7 +22,7 @@ def test_fp64_roofline_counts():
     peaks = {"dfma": {"ops_per_s": 5e11}, "drcp_in_dfma_slots": 6.0}
     r = bench.fp64_roofline(64_000, 80.0, 0.25, peaks, 2.5, 2.9)
     f_cut = (2.5 / 2.9) ** 3
-    per_pair = 6 + f_cut * (8 + 6.0)
+    per_pair = f_cut * (14 + 6.0)
     assert r["ops_per_listed_pair"] == pytest.approx(per_pair, abs=0.01)
     ops = 64_000 * (80.0 * per_pair + 13)
     assert r["ops_per_launch"] == int(ops)
