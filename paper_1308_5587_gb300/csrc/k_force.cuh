@@ -362,10 +362,18 @@ __device__ __forceinline__ void force_body(const SysDev* __restrict__ sysv,
         const double4_32a pj = pp[u];
         double dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         // minimum image: |d| < L; the test on the high words is exact except within
-        // 2^-20 of L/2, where either choice leaves |d| ~ L/2 > r_cut
-        if ((__double2hiint(dx) & 0x7fffffff) > h0) dx -= copysign(L0, dx);
-        if ((__double2hiint(dy) & 0x7fffffff) > h1) dy -= copysign(L1, dy);
-        if ((__double2hiint(dz) & 0x7fffffff) > h2) dz -= copysign(L2, dz);
+        // 2^-20 of L/2, where either choice leaves |d| ~ L/2 > r_cut.  Only pairs
+        // across a box face need it, so a warp takes the correction (FP64 adds on
+        // every lane once the compiler turns it into selects) only when one of its
+        // pairs does
+        const bool wx = (__double2hiint(dx) & 0x7fffffff) > h0;
+        const bool wy = (__double2hiint(dy) & 0x7fffffff) > h1;
+        const bool wz = (__double2hiint(dz) & 0x7fffffff) > h2;
+        if (__any_sync(__activemask(), wx || wy || wz)) {
+          if (wx) dx -= copysign(L0, dx);
+          if (wy) dy -= copysign(L1, dy);
+          if (wz) dz -= copysign(L2, dz);
+        }
         const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const PairD P = MT ? tabd[ti * nt + (int)__double_as_longlong(pj.w)] : p0;
         // both positive, so the bit patterns order like the values
