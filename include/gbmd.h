@@ -383,8 +383,11 @@ int gbmd_set_force_events(gbmd_system *s, void *ev_begin, void *ev_end);
 int gbmd_batch_create(int32_t precision, void *stream, int32_t device, gbmd_batch **out);
 
 /* Add a system (between steps only).  The system's own stream is replaced by the
- * batch's while it is a member; gbmd_step on it returns STATE.  *slot receives a
- * slot id for gbmd_batch_remove. */
+ * batch's while it is a member; gbmd_step on it returns STATE.  Its readouts
+ * (forces, thermo, state) take the batch's force tuning from then on, also after
+ * gbmd_batch_set_tuning / gbmd_batch_autotune, so that they equal those of a
+ * system stepped alone at that tuning.  *slot receives a slot id for
+ * gbmd_batch_remove. */
 int gbmd_batch_add(gbmd_batch *b, gbmd_system *s, int32_t *slot);
 
 /* Remove the system in `slot` (between steps; synchronises).  The system stays

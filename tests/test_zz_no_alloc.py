@@ -91,6 +91,7 @@ def test_noalloc_thermo_does_not_depend_on_the_force_tuning():
     # for every block size at one threads-per-particle setting
     w = wl.lj_fluid(5000, 0.84, 1.2, seed=504)
     s = gbmd.System.from_workload(w, precision="fp64")
+    s.set_tuning(2, 128)   # the reference at the lane count every block size below uses
     s.step(10)
     ref = gbmd.gbmd_get_thermo_noalloc(s.handle)
     for block in (64, 128, 256, 512):
