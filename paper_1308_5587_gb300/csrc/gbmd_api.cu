@@ -1330,8 +1330,11 @@ int autotune_group(Group* g, const char* cache) {
   }
   int best_t = g->tpp, best_b = g->fblock;
   float best = 1e30f;
+  // FP64 also tries 64-thread blocks (its best step shape from 32k particles on)
+  const bool fp64 = g->precision == GBMD_FP64;
   for (int tpp : {1, 2, 4})
-    for (int block : {128, 256, 512}) {
+    for (int block : {64, 128, 256, 512}) {
+      if (block == 64 && !fp64) continue;
       RET(set_tuning(g, tpp, block));
       float ms;
       RET(time_force(g, &ms));
