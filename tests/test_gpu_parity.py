@@ -347,6 +347,38 @@ def test_edge_cases_one_and_two_particles_and_far_images():
     s2.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pairs_at_the_cutoff_inside_and_across_the_box(prec):
+    """Two particles at r = r_cut (1 + delta), delta from -1e-5 to +1e-5, inside the
+    box and across a box face.  The FP64 path rejects a pair beyond r_cut by an FP32
+    test on the fixed-point shadow first, and corrects the minimum image only in
+    warps where some pair crosses a face: inside r_cut the forces match the oracle
+    (FP64 1e-12, mixed 1e-5), beyond it they are exactly zero.  Mixed precision
+    decides the cut in FP32, so it is held to pairs 1e-5 from r_cut."""
+    L = 12.0
+    box = np.full(3, L)
+    pairs = wl.lj_single().as_dict()
+    rc = 2.5
+    u = np.array([1.0, 0.3, -0.2])
+    u /= np.linalg.norm(u)
+    deltas = (-1e-5, -1e-6, -1e-7, -1e-9, 1e-9, 1e-7, 1e-6, 1e-5) if prec == "fp64" else (-1e-5, 1e-5)
+    for delta in deltas:
+        r = rc * (1.0 + delta)
+        for across in (False, True):
+            p0 = np.array([L / 2 - 0.4, 0.1, -0.2]) if across else np.array([-1.0, 0.5, 0.3])
+            pos = np.stack([p0, p0 + r * u])
+            s = gbmd.System(pos, np.zeros((2, 3)), box, precision=prec)
+            p = s.state()[0]
+            F = s.forces()
+            Fo, *_ = oracle.forces(p, box, np.zeros(2, np.int32), pairs)
+            if delta > 0:
+                assert np.all(F == 0) and np.all(Fo == 0), (delta, across)
+            else:
+                tol = 1e-12 if prec == "fp64" else 1e-5
+                assert rel_l2(F, Fo) <= tol, (delta, across, F, Fo)
+            s.close()
+
+
 def test_step_limit_and_async_steps():
     w = wl.lj_fluid(1000, 0.84, 1.2, seed=95)
     s = gbmd.System.from_workload(w, precision="mixed")
