@@ -379,6 +379,26 @@ def test_pairs_at_the_cutoff_inside_and_across_the_box(prec):
             s.close()
 
 
+def test_fp64_kob_andersen_at_the_one_lane_default():
+    """FP64 from 32k particles runs one lane per particle in 64-thread blocks, with
+    the two-type table of the FP32 pre-test and the FP64 coefficients in shared
+    memory: a 40,000-particle Kob-Andersen mixture, sampled particles against the
+    oracle at 1e-12, at creation and after 50 steps with rebuilds."""
+    w = wl.lj_fluid(40_000, 1.2, 1.0, seed=47, binary=True, r_buff=0.3)
+    s = gbmd.System.from_workload(w, precision="fp64")
+    info = s.info()
+    assert info["threads_per_particle"] == 1 and info["force_block"] == 64
+    idx = np.random.default_rng(6).choice(w.n, 768, replace=False)
+    for nsteps in (0, 50):
+        s.step(nsteps)
+        pos = s.state()[0]
+        F = s.forces()
+        Fo, *_ = oracle.forces_subset(pos, w.box, w.types, w.pairs.as_dict(), idx)
+        assert rel_l2(F[idx], Fo) <= 1e-12, nsteps
+    assert s.info()["n_rebuilds"] >= 1
+    s.close()
+
+
 def test_step_limit_and_async_steps():
     w = wl.lj_fluid(1000, 0.84, 1.2, seed=95)
     s = gbmd.System.from_workload(w, precision="mixed")
